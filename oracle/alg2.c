@@ -173,28 +173,37 @@ static inline int before(const graph *g, int32_t a, int32_t b) {
  * triangle count. */
 static int64_t support_forward(const graph *g, int32_t *sup) {
   memset(sup, 0, sizeof(int32_t) * (size_t)g->m);
+  /* later-neighbour lists A(v) = {w in nb(v) : v before w}, with edge ids */
+  int64_t *aoff = (int64_t *)calloc((size_t)g->n + 1, sizeof(int64_t));
+  int32_t *aw = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->m + 1));
+  int32_t *ae = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->m + 1));
   int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n + 1));
+  for (int32_t v = 0; v < (int32_t)g->n; v++) {
+    aoff[v + 1] = aoff[v];
+    for (int64_t j = g->off[v]; j < g->off[v + 1]; j++)
+      if (before(g, v, g->adj[j])) {
+        aw[aoff[v + 1]] = g->adj[j];
+        ae[aoff[v + 1]++] = g->adje[j];
+      }
+  }
   for (int64_t v = 0; v < g->n; v++) mark[v] = -1;
   int64_t tri = 0;
   for (int32_t u = 0; u < (int32_t)g->n; u++) {
-    for (int64_t j = g->off[u]; j < g->off[u + 1]; j++)
-      if (before(g, u, g->adj[j])) mark[g->adj[j]] = g->adje[j];   /* mark[w] = e_uw */
-    for (int64_t j = g->off[u]; j < g->off[u + 1]; j++) {
-      int32_t v = g->adj[j];
-      if (!before(g, u, v)) continue;
-      int32_t e_uv = g->adje[j];
-      for (int64_t q = g->off[v]; q < g->off[v + 1]; q++) {
-        int32_t w = g->adj[q];
-        if (!before(g, v, w) || mark[w] < 0) continue;
+    for (int64_t j = aoff[u]; j < aoff[u + 1]; j++) mark[aw[j]] = ae[j];  /* mark[w] = e_uw */
+    for (int64_t j = aoff[u]; j < aoff[u + 1]; j++) {
+      int32_t v = aw[j], e_uv = ae[j];
+      for (int64_t q = aoff[v]; q < aoff[v + 1]; q++) {
+        int32_t w = aw[q];
+        if (mark[w] < 0) continue;
         sup[e_uv]++;
         sup[mark[w]]++;      /* e_uw */
-        sup[g->adje[q]]++;   /* e_vw */
+        sup[ae[q]]++;        /* e_vw */
         tri++;
       }
     }
-    for (int64_t j = g->off[u]; j < g->off[u + 1]; j++) mark[g->adj[j]] = -1;
+    for (int64_t j = aoff[u]; j < aoff[u + 1]; j++) mark[aw[j]] = -1;
   }
-  free(mark);
+  free(aoff); free(aw); free(ae); free(mark);
   return tri;
 }
 
