@@ -1,0 +1,148 @@
+/*
+ * truss.h -- C ABI of the GB300 (sm_103a) exact truss-decomposition library.
+ *
+ * Problem (Wang & Cheng, "Truss Decomposition in Massive Networks", Section 2,
+ * problem definition): for an undirected simple graph G, compute for every edge
+ * e its support sup(e) -- the number of triangles of G containing e
+ * (Definition 1) -- and its truss number phi(e) = max{k : e in T_k}, where the
+ * k-truss T_k is the largest subgraph in which every edge lies in at least k-2
+ * triangles (Definition 2).  The k-class Phi_k (Definition 3) is the set of
+ * edges with phi(e) = k, so the per-edge truss numbers are the whole
+ * decomposition.  The method follows Algorithm 2 (Section 3.2): supports first
+ * (step 2), then edges are removed in ascending order of support, decrementing
+ * the support of the other two edges of each destroyed triangle (steps 4-12).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Input is an edge list of `rows` rows: src[r], dst[r] are int32 vertex ids
+ *   in [0, n).  Rows are undirected pairs in either orientation; duplicate and
+ *   reversed rows are allowed and receive the values of their edge; a self-loop
+ *   row (src == dst) receives -1 in every per-row output.
+ * - After removing self-loops and duplicates the number of distinct edges m
+ *   must be < 2^31 (edge ids are int32).  n must be < 2^31.
+ * - Every per-row output is indexed by input row and is int32.
+ * - Pointers may be device memory or host memory (pageable or pinned); the
+ *   library detects which with cudaPointerGetAttributes and stages host
+ *   buffers through device memory it owns.  The caller owns every input and
+ *   output buffer; the library owns its workspace (a per-context arena that
+ *   grows on demand and is released by truss_ctx_destroy).
+ * - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Work
+ *   is enqueued on it; the call reads two small counters back from the device
+ *   (the number of distinct edges and the number of triangles, to size the
+ *   workspace), so it returns only after the outputs are complete.
+ * - Return value: TRUSS_OK (0) or a negative TRUSS_E* code; nothing throws
+ *   across the ABI.  On error the outputs are unspecified.
+ * - A truss_ctx is not thread-safe: use one context per host thread.  The
+ *   truss_serve_* functions below are thread-safe.
+ */
+#ifndef TRUSS_H
+#define TRUSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- errors --- */
+#define TRUSS_OK 0
+#define TRUSS_EINVAL (-1)    /* bad argument, vertex id out of [0, n), m >= 2^31 */
+#define TRUSS_ENOMEM (-2)    /* device or host allocation failed */
+#define TRUSS_ECUDA (-3)     /* a CUDA runtime call failed */
+#define TRUSS_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define TRUSS_EAGAIN (-5)    /* serve: result not ready yet */
+#define TRUSS_EBUSY (-6)     /* serve: admission refused (queue full / over budget) */
+#define TRUSS_ESHUTDOWN (-7) /* serve: server stopped */
+#define TRUSS_ECHECK (-8)    /* an internal consistency check failed */
+
+/* Human-readable message for a TRUSS_* code (static storage). */
+const char *truss_strerror(int code);
+
+/* ------------------------------------------------------------ context --- */
+typedef struct truss_ctx truss_ctx;
+
+typedef struct truss_opts {
+  /* Upper limit, in nanoseconds, of any device-side wait (the grid-wide
+   * barrier of the persistent peel kernel).  A wait that exceeds it makes the
+   * call return TRUSS_ETIMEOUT.  0 = default (4 s). */
+  int64_t wait_limit_ns;
+  /* Non-zero: record CUDA events around each stage (build, support, triangle
+   * lists, peel, scatter) so truss_last_stats reports stage times. */
+  int32_t profile;
+  /* Non-zero: also compute the algorithmic byte counts of the support and
+   * peel kernels (one extra host pass over small arrays). */
+  int32_t count_bytes;
+  /* Threads per block of the support/list kernels (0 = tuned default). */
+  int32_t support_block;
+  /* Resident blocks per SM of the persistent peel kernel (0 = occupancy max). */
+  int32_t peel_blocks_per_sm;
+  /* Frontier size at or below which the peel runs a level's sub-rounds inside
+   * one block (block barriers instead of grid barriers).  <0 disables, 0 =
+   * tuned default. */
+  int32_t peel_small_frontier;
+  int32_t reserved[8];
+} truss_opts;
+
+/* Create a context bound to CUDA device `device` (ordinal).  opts may be NULL
+ * (all defaults).  *out receives the context.  Errors: TRUSS_EINVAL (bad
+ * device or NULL out), TRUSS_ECUDA, TRUSS_ENOMEM. */
+int truss_ctx_create(truss_ctx **out, int device, const truss_opts *opts);
+
+/* Release the context and its workspace.  NULL is accepted. */
+int truss_ctx_destroy(truss_ctx *ctx);
+
+/* ------------------------------------------------------- single graph --- */
+/* Support of every edge (Definition 1; Algorithm 2 step 2).
+ * n: vertex count; rows: number of rows of src/dst (0 allowed).
+ * support_out[r] = sup(e) of row r's edge, -1 for self-loop rows.
+ * Errors: TRUSS_EINVAL, TRUSS_ENOMEM, TRUSS_ECUDA. */
+int truss_support(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                  const int32_t *dst, int32_t *support_out, void *cuda_stream);
+
+/* Full truss decomposition (Algorithm 2; Definitions 1-3).
+ * support_out (nullable): sup(e) per row, as truss_support.
+ * truss_out: phi(e) per row (>= 2), -1 for self-loop rows.
+ * kmax_out (nullable, host or device int32[1]): k_max = max phi (0 if the
+ * graph has no edge).
+ * Errors: TRUSS_EINVAL, TRUSS_ENOMEM, TRUSS_ECUDA, TRUSS_ETIMEOUT. */
+int truss_decompose(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                    const int32_t *dst, int32_t *support_out, int32_t *truss_out,
+                    int32_t *kmax_out, void *cuda_stream);
+
+/* ------------------------------------------------------------- batched --- */
+/* Decompose G independent graphs in one pass.  Graph g has n[g] vertices and
+ * rows row_off[g] .. row_off[g+1]-1 of src/dst, with ids local to the graph
+ * (in [0, n[g])).  row_off has G+1 entries, row_off[0] = 0, non-decreasing.
+ * n and row_off are HOST arrays.  Per-row outputs are as truss_decompose over
+ * the concatenated rows; kmax_out (nullable, host or device int32[G]) receives
+ * each graph's k_max.  The result for each graph equals truss_decompose on
+ * that graph alone: the truss numbers of a disjoint union are those of its
+ * components (Definition 2).  Errors as truss_decompose. */
+int truss_decompose_batch(truss_ctx *ctx, int32_t G, const int64_t *n, const int64_t *row_off,
+                          const int32_t *src, const int32_t *dst, int32_t *support_out,
+                          int32_t *truss_out, int32_t *kmax_out, void *cuda_stream);
+
+/* --------------------------------------------------------------- stats --- */
+typedef struct truss_run_stats {
+  int64_t n, rows, m;        /* vertices, input rows, distinct edges */
+  int64_t triangles;         /* |triangles of G| = sum sup / 3 */
+  int32_t kmax;              /* max truss number */
+  int32_t levels;            /* levels k with a non-empty scan */
+  int32_t subrounds;         /* peel sub-rounds over all levels */
+  int32_t graphs;            /* 1, or G for a batch */
+  /* stage times in ms (profile != 0), else 0 */
+  float ms_build, ms_support, ms_lists, ms_peel, ms_scatter, ms_total;
+  /* algorithmic bytes (count_bytes != 0), else 0: see DESIGN notes in the
+   * library sources for the per-unit figures */
+  double bytes_support, bytes_lists, bytes_peel;
+  /* kernels this call launched (own kernels plus the CUB sort/scan passes) */
+  int64_t launches;
+} truss_run_stats;
+
+/* Statistics of the last successful call on this context. */
+int truss_last_stats(truss_ctx *ctx, truss_run_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRUSS_H */

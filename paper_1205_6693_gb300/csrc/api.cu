@@ -1,0 +1,445 @@
+// C ABI of the truss library (include/truss.h): contexts, argument checks,
+// host/device staging, and the single-graph / batched pipelines.
+//
+// Pipeline of one call (all kernels on the caller's stream):
+//   build_csr   rows -> degree-ordered oriented CSR, row -> edge id
+//   run_support sup(e) (Definition 1, Algorithm 2 step 2)
+//   run_lists   per-edge triangle lists (edge-id pairs)
+//   run_peel    truss numbers (Algorithm 2 steps 3-16), one persistent launch
+//   scatter     per-row outputs
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+struct truss_ctx {
+  int device = 0;
+  truss_opts opts{};
+  tr::Arena arena;
+  int32_t *d_err = nullptr;  // device error word for argument checks
+  truss_run_stats last{};
+  cudaEvent_t ev[8] = {};
+  bool have_events = false;
+  int sms = 0;
+};
+
+namespace tr {
+
+namespace {
+thread_local std::string g_last_cuda_error;
+thread_local int64_t g_launches = 0;
+}
+
+void count_launches(int k) { g_launches += k; }
+int64_t take_launches() {
+  int64_t v = g_launches;
+  g_launches = 0;
+  return v;
+}
+
+void note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_cuda_error = buf;
+  if (getenv("TRUSS_VERBOSE")) fprintf(stderr, "[truss] %s\n", buf);
+}
+
+// ------------------------------------------------------------------ Arena ---
+Arena::~Arena() { release_all(); }
+
+void Arena::release_all() {
+  for (auto &c : chunks_) cudaFree(c.p);
+  chunks_.clear();
+}
+
+void Arena::reset() {
+  for (auto &c : chunks_) c.used = 0;
+}
+
+size_t Arena::reserved() const {
+  size_t s = 0;
+  for (auto &c : chunks_) s += c.cap;
+  return s;
+}
+
+void *Arena::alloc(size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes == 0) bytes = 256;
+  for (auto &c : chunks_) {
+    if (c.cap - c.used >= bytes) {
+      void *p = c.p + c.used;
+      c.used += bytes;
+      return p;
+    }
+  }
+  size_t cap = bytes < ((size_t)64 << 20) ? ((size_t)64 << 20) : bytes;
+  char *p = nullptr;
+  if (cudaMalloc(&p, cap) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    return nullptr;
+  }
+  chunks_.push_back(Chunk{p, cap, bytes});
+  return p;
+}
+
+// ------------------------------------------------------------ scatter ---
+namespace {
+__global__ void k_scatter(int64_t rows, const int32_t *row2e, const int32_t *sup,
+                          const int32_t *truss, int32_t *sup_rows, int32_t *truss_rows) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = row2e[r];
+    if (sup_rows) sup_rows[r] = e < 0 ? -1 : sup[e];
+    if (truss_rows) truss_rows[r] = e < 0 ? -1 : truss[e];
+  }
+}
+
+// One block per graph: k_max = max truss number over its rows.
+__global__ void k_batch_kmax(int32_t G, const int64_t *row_off, const int32_t *truss_rows,
+                             int32_t *kmax) {
+  __shared__ int red[32];
+  for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    int best = 0;
+    for (int64_t r = row_off[g] + threadIdx.x; r < row_off[g + 1]; r += blockDim.x)
+      best = max(best, truss_rows[r]);
+    best = __reduce_max_sync(TR_FULL, best);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+      v = __reduce_max_sync(TR_FULL, v);
+      if (threadIdx.x == 0) kmax[g] = v;
+    }
+    __syncthreads();
+  }
+}
+}  // namespace
+
+int scatter_rows(const Csr &g, const int32_t *sup, const int32_t *truss, int32_t *sup_rows,
+                 int32_t *truss_rows, cudaStream_t s) {
+  if (g.rows == 0) return TRUSS_OK;
+  k_scatter<<<grid_for(g.rows, 256, 152 * 16), 256, 0, s>>>(g.rows, g.row2e, sup, truss, sup_rows,
+                                                             truss_rows);
+  TR_LAUNCHED();
+  return TRUSS_OK;
+}
+
+int batch_kmax(int32_t G, const int64_t *row_off, const int32_t *truss_rows, int32_t *kmax,
+               cudaStream_t s) {
+  if (G <= 0) return TRUSS_OK;
+  k_batch_kmax<<<G < 4096 ? G : 4096, 256, 0, s>>>(G, row_off, truss_rows, kmax);
+  TR_LAUNCHED();
+  return TRUSS_OK;
+}
+
+}  // namespace tr
+
+// ================================================================== C ABI ===
+namespace {
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+int stage_in(tr::Arena &A, const T *p, int64_t count, const T **out, cudaStream_t s) {
+  if (count == 0 || p == nullptr || is_device_ptr(p)) {
+    *out = p;
+    return TRUSS_OK;
+  }
+  T *d = A.get<T>(count);
+  if (!d) return TRUSS_ENOMEM;
+  TR_CUDA(cudaMemcpyAsync(d, p, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+  *out = d;
+  return TRUSS_OK;
+}
+
+struct OutBuf {
+  int32_t *user = nullptr;
+  int32_t *dev = nullptr;
+  bool host = false;
+};
+
+int stage_out(tr::Arena &A, int32_t *user, int64_t count, OutBuf *o) {
+  o->user = user;
+  o->host = false;
+  o->dev = user;
+  if (!user) return TRUSS_OK;
+  if (!is_device_ptr(user)) {
+    o->host = true;
+    o->dev = A.get<int32_t>(count);
+    if (!o->dev) return TRUSS_ENOMEM;
+  }
+  return TRUSS_OK;
+}
+
+int copy_back(const OutBuf &o, int64_t count, cudaStream_t s) {
+  if (o.user && o.host && count > 0)
+    TR_CUDA(cudaMemcpyAsync(o.user, o.dev, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
+  return TRUSS_OK;
+}
+
+struct Stage {
+  truss_ctx *c;
+  cudaStream_t s;
+  int next = 0;
+  void mark() {
+    if (c->opts.profile && c->have_events && next < 8) cudaEventRecord(c->ev[next++], s);
+  }
+  float ms(int a, int b) const {
+    float t = 0.f;
+    if (b < next && a < b) cudaEventElapsedTime(&t, c->ev[a], c->ev[b]);
+    return t;
+  }
+};
+
+int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *src,
+                 const int32_t *dst, int32_t G, const int64_t *h_row_off, const int64_t *h_voff,
+                 int32_t *support_out, int32_t *truss_out, int32_t *kmax_out, bool want_truss,
+                 cudaStream_t s) {
+  TR_CUDA(cudaSetDevice(ctx->device));
+  tr::Arena &A = ctx->arena;
+  A.reset();
+  tr::take_launches();
+  truss_run_stats st{};
+  st.n = n_total;
+  st.rows = rows;
+  st.graphs = G;
+  Stage sg{ctx, s};
+  sg.mark();  // 0
+
+  tr::RowsIn in;
+  in.rows = rows;
+  in.n = n_total;
+  TR_TRY(stage_in(A, src, rows, &in.src, s));
+  TR_TRY(stage_in(A, dst, rows, &in.dst, s));
+  int64_t *d_row_off = nullptr, *d_voff = nullptr;
+  if (h_row_off) {
+    d_row_off = A.get<int64_t>(G + 1);
+    d_voff = A.get<int64_t>(G + 1);
+    if (!d_row_off || !d_voff) return TRUSS_ENOMEM;
+    TR_CUDA(cudaMemcpyAsync(d_row_off, h_row_off, sizeof(int64_t) * (G + 1),
+                            cudaMemcpyHostToDevice, s));
+    TR_CUDA(cudaMemcpyAsync(d_voff, h_voff, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice,
+                            s));
+    in.graphs = G;
+    in.row_off = d_row_off;
+    in.voff = d_voff;
+  }
+  TR_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
+
+  tr::Csr g;
+  TR_TRY(tr::build_csr(A, in, &g, ctx->d_err, s));
+  sg.mark();  // 1
+  st.m = g.m;
+
+  tr::SupportCfg scfg;
+  scfg.sms = ctx->sms;
+  tr::SupportOut so;
+  TR_TRY(tr::run_support(A, g, scfg, &so, s));
+  sg.mark();  // 2
+  st.triangles = so.entries / 3;
+
+  int32_t *truss_e = nullptr;
+  tr::PeelResult pr;
+  if (want_truss) {
+    int2 *pairs = A.get<int2>(so.entries);
+    truss_e = A.get<int32_t>(g.m);
+    if (!pairs || !truss_e) return TRUSS_ENOMEM;
+    TR_TRY(tr::run_lists(A, g, scfg, so, pairs, s));
+    sg.mark();  // 3
+    tr::PeelCfg pcfg;
+    pcfg.sms = ctx->sms;
+    pcfg.blocks_per_sm = ctx->opts.peel_blocks_per_sm;
+    pcfg.small_frontier = ctx->opts.peel_small_frontier;
+    if (ctx->opts.wait_limit_ns > 0) pcfg.wait_ns = ctx->opts.wait_limit_ns;
+    int rc = tr::run_peel(A, g, so, pairs, pcfg, truss_e, &pr, s);
+    if (rc != TRUSS_OK) return rc;
+    sg.mark();  // 4
+    st.kmax = pr.kmax;
+    st.levels = pr.levels;
+    st.subrounds = pr.subrounds;
+  }
+
+  OutBuf os, ot;
+  TR_TRY(stage_out(A, support_out, rows, &os));
+  TR_TRY(stage_out(A, want_truss ? truss_out : nullptr, rows, &ot));
+  TR_TRY(tr::scatter_rows(g, so.sup, truss_e, os.dev, ot.dev, s));
+  if (G > 1 || h_row_off) {
+    if (kmax_out && want_truss) {
+      OutBuf ok;
+      TR_TRY(stage_out(A, kmax_out, G, &ok));
+      TR_TRY(tr::batch_kmax(G, d_row_off, ot.dev, ok.dev, s));
+      TR_TRY(copy_back(ok, G, s));
+    }
+  }
+  TR_TRY(copy_back(os, rows, s));
+  TR_TRY(copy_back(ot, rows, s));
+  sg.mark();  // 5 (or 3 for support only)
+  int32_t k_host = pr.kmax;
+  if (!(G > 1 || h_row_off) && kmax_out && want_truss) {
+    if (is_device_ptr(kmax_out)) {
+      TR_CUDA(cudaMemcpyAsync(kmax_out, &k_host, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    } else {
+      *kmax_out = k_host;
+    }
+  }
+  TR_CUDA(cudaStreamSynchronize(s));
+  if (ctx->opts.profile && ctx->have_events) {
+    st.ms_build = sg.ms(0, 1);
+    st.ms_support = sg.ms(1, 2);
+    if (want_truss) {
+      st.ms_lists = sg.ms(2, 3);
+      st.ms_peel = sg.ms(3, 4);
+      st.ms_scatter = sg.ms(4, 5);
+      st.ms_total = sg.ms(0, 5);
+    } else {
+      st.ms_scatter = sg.ms(2, 3);
+      st.ms_total = sg.ms(0, 3);
+    }
+  }
+  st.launches = tr::take_launches();
+  if (ctx->opts.count_bytes) {
+    double bs = 0, bl = 0;
+    TR_TRY(tr::count_support_bytes(A, g, st.triangles, &bs, &bl, s));
+    st.bytes_support = bs;
+    st.bytes_lists = want_truss ? bl : 0.0;
+    if (want_truss)
+      st.bytes_peel = 28.0 * (double)g.m + 16.0 * (double)pr.entries +
+                      8.0 * (double)pr.decrements + 16.0 * (double)pr.scanned;
+  }
+  ctx->last = st;
+  return TRUSS_OK;
+}
+
+int check_common(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst) {
+  if (!ctx) return TRUSS_EINVAL;
+  if (n < 0 || n >= ((int64_t)1 << 31)) return TRUSS_EINVAL;
+  if (rows < 0 || rows >= ((int64_t)1 << 31)) return TRUSS_EINVAL;
+  if (rows > 0 && (!src || !dst)) return TRUSS_EINVAL;
+  if (rows > 0 && n == 0) return TRUSS_EINVAL;
+  return TRUSS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *truss_strerror(int code) {
+  switch (code) {
+    case TRUSS_OK: return "ok";
+    case TRUSS_EINVAL: return "invalid argument (bad size, null pointer or vertex id out of range)";
+    case TRUSS_ENOMEM: return "out of memory";
+    case TRUSS_ECUDA: return "CUDA runtime error";
+    case TRUSS_ETIMEOUT: return "a bounded device-side wait timed out";
+    case TRUSS_EAGAIN: return "result not ready";
+    case TRUSS_EBUSY: return "admission refused (queue full or over memory budget)";
+    case TRUSS_ESHUTDOWN: return "server stopped";
+    case TRUSS_ECHECK: return "internal consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+int truss_ctx_create(truss_ctx **out, int device, const truss_opts *opts) {
+  if (!out) return TRUSS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return TRUSS_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return TRUSS_EINVAL;
+  truss_ctx *c = new (std::nothrow) truss_ctx();
+  if (!c) return TRUSS_ENOMEM;
+  c->device = device;
+  if (opts) c->opts = *opts;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&c->d_err, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return TRUSS_ECUDA;
+  }
+  bool ok = true;
+  for (auto &e : c->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+  c->have_events = ok;
+  *out = c;
+  return TRUSS_OK;
+}
+
+int truss_ctx_destroy(truss_ctx *ctx) {
+  if (!ctx) return TRUSS_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->have_events)
+    for (auto &e : ctx->ev) cudaEventDestroy(e);
+  cudaFree(ctx->d_err);
+  ctx->arena.release_all();
+  delete ctx;
+  return TRUSS_OK;
+}
+
+int truss_support(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+                  int32_t *support_out, void *cuda_stream) {
+  TR_TRY(check_common(ctx, n, rows, src, dst));
+  if (rows > 0 && !support_out) return TRUSS_EINVAL;
+  return run_pipeline(ctx, n, rows, src, dst, 1, nullptr, nullptr, support_out, nullptr, nullptr,
+                      false, (cudaStream_t)cuda_stream);
+}
+
+int truss_decompose(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                    const int32_t *dst, int32_t *support_out, int32_t *truss_out,
+                    int32_t *kmax_out, void *cuda_stream) {
+  TR_TRY(check_common(ctx, n, rows, src, dst));
+  if (rows > 0 && !truss_out) return TRUSS_EINVAL;
+  return run_pipeline(ctx, n, rows, src, dst, 1, nullptr, nullptr, support_out, truss_out,
+                      kmax_out, true, (cudaStream_t)cuda_stream);
+}
+
+int truss_decompose_batch(truss_ctx *ctx, int32_t G, const int64_t *n, const int64_t *row_off,
+                          const int32_t *src, const int32_t *dst, int32_t *support_out,
+                          int32_t *truss_out, int32_t *kmax_out, void *cuda_stream) {
+  if (!ctx || G < 0 || (G > 0 && (!n || !row_off))) return TRUSS_EINVAL;
+  if (G == 0) return TRUSS_OK;
+  if (row_off[0] != 0) return TRUSS_EINVAL;
+  std::vector<int64_t> voff((size_t)G + 1, 0);
+  for (int32_t g = 0; g < G; g++) {
+    if (n[g] < 0 || row_off[g + 1] < row_off[g]) return TRUSS_EINVAL;
+    if (row_off[g + 1] > row_off[g] && n[g] == 0) return TRUSS_EINVAL;
+    voff[g + 1] = voff[g] + n[g];
+  }
+  const int64_t rows = row_off[G], ntot = voff[G];
+  TR_TRY(check_common(ctx, ntot > 0 ? ntot : 1, rows, src, dst));
+  if (rows > 0 && !truss_out) return TRUSS_EINVAL;
+  if (rows == 0) {
+    if (kmax_out) {
+      std::vector<int32_t> z((size_t)G, 0);
+      if (is_device_ptr(kmax_out)) {
+        TR_CUDA(cudaMemcpy(kmax_out, z.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice));
+      } else {
+        memcpy(kmax_out, z.data(), sizeof(int32_t) * G);
+      }
+    }
+    return TRUSS_OK;
+  }
+  return run_pipeline(ctx, ntot, rows, src, dst, G, row_off, voff.data(), support_out, truss_out,
+                      kmax_out, true, (cudaStream_t)cuda_stream);
+}
+
+int truss_last_stats(truss_ctx *ctx, truss_run_stats *out) {
+  if (!ctx || !out) return TRUSS_EINVAL;
+  *out = ctx->last;
+  return TRUSS_OK;
+}
+
+}  // extern "C"

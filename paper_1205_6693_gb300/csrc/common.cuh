@@ -1,0 +1,112 @@
+// Shared device/host helpers of the truss library (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/truss.h"
+
+#define TR_FULL 0xffffffffu
+
+namespace tr {
+
+// ------------------------------------------------------------------ host ---
+// Evaluate a CUDA runtime call; on failure return TRUSS_ECUDA from the
+// enclosing function (remembering the message for diagnostics).
+void note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void count_launches(int k);
+
+#define TR_CUDA(call)                                             \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      ::tr::note_cuda_error(e_, #call, __FILE__, __LINE__);       \
+      return e_ == cudaErrorMemoryAllocation ? TRUSS_ENOMEM : TRUSS_ECUDA; \
+    }                                                             \
+  } while (0)
+
+// After a kernel launch: count it and check the launch error.
+#define TR_LAUNCHED()                  \
+  do {                                 \
+    ::tr::count_launches(1);           \
+    TR_CUDA(cudaGetLastError());       \
+  } while (0)
+
+#define TR_TRY(expr)          \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != TRUSS_OK) return rc_; \
+  } while (0)
+
+inline int grid_for(int64_t work, int block, int max_blocks) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+inline int bits_for(uint64_t maxval) {  // number of bits to represent maxval
+  int b = 0;
+  while (b < 64 && (maxval >> b) != 0) b++;
+  return b;
+}
+
+// ---------------------------------------------------------------- device ---
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Inclusive prefix sum across the warp.
+__device__ __forceinline__ int warp_incl_scan(int x) {
+  const int l = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(TR_FULL, x, o);
+    if (l >= o) x += y;
+  }
+  return x;
+}
+
+// Smallest lane o such that P[o] > t, for a non-decreasing per-lane value P
+// with t < P[31].  All 32 lanes must call it.
+__device__ __forceinline__ int warp_owner(int P, int t) {
+  int o = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    int pv = __shfl_sync(TR_FULL, P, o + s - 1);
+    if (pv <= t) o += s;
+  }
+  return o;
+}
+
+// Warp-aggregated append: every lane with `pred` gets a distinct slot in a
+// buffer whose fill counter is *cnt; returns the slot (or -1).  All lanes of
+// the warp must call it.
+__device__ __forceinline__ int warp_append(bool pred, int *cnt) {
+  unsigned mask = __ballot_sync(TR_FULL, pred);
+  if (mask == 0) return -1;
+  int leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane_id() == leader) base = atomicAdd(cnt, __popc(mask));
+  base = __shfl_sync(TR_FULL, base, leader);
+  if (!pred) return -1;
+  return base + __popc(mask & ((1u << lane_id()) - 1u));
+}
+
+// As warp_append, for a monotonically increasing 64-bit counter: returns the
+// counter value reserved for this lane (the caller subtracts its base).
+__device__ __forceinline__ long long warp_append64(bool pred, unsigned long long *cnt) {
+  unsigned mask = __ballot_sync(TR_FULL, pred);
+  if (mask == 0) return -1;
+  int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane_id() == leader) base = atomicAdd(cnt, (unsigned long long)__popc(mask));
+  base = __shfl_sync(TR_FULL, base, leader);
+  if (!pred) return -1;
+  return (long long)(base + __popc(mask & ((1u << lane_id()) - 1u)));
+}
+
+}  // namespace tr

@@ -1,0 +1,133 @@
+// Internal host-side interfaces between the translation units of the truss
+// library.  Nothing here crosses the C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tr {
+
+// Kernels launched by the calling host thread since the last reset (own
+// kernels counted at each launch site, CUB calls by their pass count).
+void count_launches(int k);
+int64_t take_launches();
+
+// Device workspace: a list of cudaMalloc'd chunks handed out by bump
+// allocation.  reset() makes every chunk reusable without freeing it, so a
+// steady stream of calls of similar size allocates nothing after the first.
+class Arena {
+ public:
+  ~Arena();
+  void reset();
+  // 256-byte aligned block, or nullptr if the device is out of memory.
+  void *alloc(size_t bytes);
+  template <class T>
+  T *get(int64_t count) {
+    return static_cast<T *>(alloc(sizeof(T) * (size_t)(count > 0 ? count : 1)));
+  }
+  size_t reserved() const;
+  void release_all();
+
+ private:
+  struct Chunk {
+    char *p;
+    size_t cap, used;
+  };
+  std::vector<Chunk> chunks_;
+};
+
+// ------------------------------------------------------------ CUB glue ---
+// Thin wrappers around CUB's device-wide radix sort / scan (cub_ops.cu).
+// `tmp` == nullptr queries the scratch size into *tmp_bytes.
+int sort_pairs_u64(void *tmp, size_t *tmp_bytes, const uint64_t *kin, uint64_t *kout,
+                   const int32_t *vin, int32_t *vout, int64_t n, int begin_bit, int end_bit,
+                   cudaStream_t s);
+int sort_pairs_u32(void *tmp, size_t *tmp_bytes, const uint32_t *kin, uint32_t *kout,
+                   const int32_t *vin, int32_t *vout, int64_t n, int begin_bit, int end_bit,
+                   cudaStream_t s);
+int inclusive_sum_i32(void *tmp, size_t *tmp_bytes, const int32_t *in, int32_t *out, int64_t n,
+                      cudaStream_t s);
+int exclusive_sum_i64(void *tmp, size_t *tmp_bytes, const int64_t *in, int64_t *out, int64_t n,
+                      cudaStream_t s);
+
+// ---------------------------------------------------------- CSR build ---
+// Input rows as seen by the device (already staged into device memory).
+struct RowsIn {
+  int64_t rows = 0;
+  int64_t n = 0;                 // total vertex count (sum over graphs for a batch)
+  const int32_t *src = nullptr;  // device
+  const int32_t *dst = nullptr;  // device
+  // batch: G graphs, device arrays row_off[G+1], voff[G+1] (vertex offsets)
+  int32_t graphs = 1;
+  const int64_t *row_off = nullptr;
+  const int64_t *voff = nullptr;
+};
+
+// Degree-ordered oriented CSR (vertices relabelled by ascending (degree, id)
+// so that an edge points from its lower-ranked to its higher-ranked end).
+// Canonical edge id e = position in adjp.
+struct Csr {
+  int64_t n = 0, m = 0, rows = 0;
+  int64_t *offp = nullptr;   // [n+1] out-list offsets (new labels)
+  int32_t *adjp = nullptr;   // [m]   head (higher-ranked endpoint) of edge e
+  int32_t *esrc = nullptr;   // [m]   tail (lower-ranked endpoint) of edge e
+  int32_t *row2e = nullptr;  // [rows] row -> e, -1 for self-loop rows
+};
+
+struct DevCounters;  // device scratch for small counters (api.cu)
+
+int build_csr(Arena &A, const RowsIn &in, Csr *out, int32_t *d_err, cudaStream_t s);
+
+// ------------------------------------------------------------- support ---
+struct SupportOut {
+  int32_t *sup = nullptr;    // [m]  sup(e)
+  int32_t *supA = nullptr;   // [m]  triangles in which e is found from its own tail
+  int64_t *toff = nullptr;   // [m+1] triangle-list offsets (exclusive sum of sup)
+  int64_t *wpre = nullptr;   // [m+1] exclusive prefix of the per-edge walk cost
+  int64_t walk = 0;          // total walk cost (entries of out-lists scanned)
+  int64_t entries = 0;       // sum sup = 3 * triangles
+};
+
+struct SupportCfg {
+  int block = 256;
+  int sms = 0;
+};
+
+// Support of every edge: sup = supA + supB (support.cu).
+int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, cudaStream_t s);
+// Triangle lists: pairs[toff[e] .. toff[e]+sup[e]) = the other two edge ids
+// of each triangle of e (support.cu).
+int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &so, int2 *pairs,
+              cudaStream_t s);
+
+// ---------------------------------------------------------------- peel ---
+struct PeelCfg {
+  int block = 512;
+  int blocks_per_sm = 0;
+  int sms = 0;
+  int small_frontier = 0;
+  long long wait_ns = 4000000000LL;
+};
+
+struct PeelResult {
+  int32_t kmax = 0, levels = 0, subrounds = 0, err = 0;
+  unsigned long long entries = 0, decrements = 0, scanned = 0;
+};
+
+int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, const PeelCfg &cfg,
+             int32_t *truss, PeelResult *res, cudaStream_t s);
+
+// -------------------------------------------------------------- outputs ---
+int scatter_rows(const Csr &g, const int32_t *sup, const int32_t *truss, int32_t *sup_rows,
+                 int32_t *truss_rows, cudaStream_t s);
+int batch_kmax(int32_t G, const int64_t *row_off, const int32_t *truss_rows, int32_t *kmax,
+               cudaStream_t s);
+
+// Algorithmic byte counts (see the comments in support.cu / peel.cu).
+int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, double *b_sup,
+                        double *b_lists, cudaStream_t s);
+
+}  // namespace tr

@@ -1,0 +1,409 @@
+// Edge support (Definition 1; Algorithm 2 step 2) and per-edge triangle lists.
+//
+// Triangles are listed once each, from their lowest-ranked vertex u in the
+// (degree, id) order (the in-memory triangle listing the paper cites for step
+// 2, with the out-list bound of Theorem 1): for v in out(u), every w in
+// out(v) that is also in out(u) closes the triangle (u, v, w), whose edges
+// are e_uv, e_uw (both in u's out-list) and e_vw (in v's out-list).
+//
+// Work is split evenly: the walk of edge (u, v) costs |out(v)|, so the
+// oriented edges are cut into ranges of equal total cost (prefix sum plus a
+// binary search per range) and warps take ranges round-robin.  For each
+// vertex u its range touches, the warp stages out(u) in shared memory (if it
+// fits in kWarpCap entries; otherwise it reads it from global memory) and
+// walks the concatenation of the lists out(v), v in its part of out(u), with
+// all 32 lanes busy: a warp prefix sum over the list lengths maps each lane's
+// flat position to (v, position in out(v)).  Membership of w in out(u) is a
+// binary search with a fixed number of steps.
+//
+// Counts are split by who can see them: supA[e] (e in out(u)) collects the
+// triangles found while u is processed -- in shared memory, then stored once
+// (or added, when u's out-list is shared by several ranges) -- and supB[e]
+// collects, by global atomics, the triangles in which e is the (v, w) edge.
+// sup = supA + supB.
+//
+// The second pass (MODE 1) repeats the walk and writes, for every triangle,
+// one entry (the other two edge ids) into each of its three edges' lists:
+// list(e) = pairs[toff[e] .. toff[e] + sup[e]), the first supA[e] entries
+// from the walk of e's tail (shared-memory cursors when one warp walks all of
+// the tail's out-list, else global cursors curA), the rest from global
+// cursors curB.
+#include "engine.h"
+
+namespace tr {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int64_t kRangeWork = 16384;  // target walk cost per range
+// Out-list entries staged per warp: counting pass (int32 counters) and list
+// pass (int64 cursors).
+template <int MODE>
+struct Cap {
+  static constexpr int value = MODE == 0 ? 512 : 256;
+};
+template <int MODE>
+__host__ __device__ constexpr size_t warp_smem() {
+  // L (int32) and counters (int32) or cursors (int64)
+  return (size_t)Cap<MODE>::value * (4 + (MODE == 0 ? 4 : 8));
+}
+
+struct SupArgs {
+  int64_t n, m;
+  const int64_t *offp;
+  const int32_t *adjp;
+  const int32_t *esrc;
+  const int64_t *wpre;  // [m+1] exclusive prefix of the walk cost per edge
+  int64_t W;            // total walk cost
+  int64_t P;            // number of ranges
+  int32_t *supA;        // MODE 0: owner counts; MODE 1: read
+  int32_t *supB;        // MODE 0: (v, w)-edge counts
+  unsigned long long *curA;  // MODE 1: next slot of e's owner part (starts at toff[e])
+  unsigned long long *curB;  // MODE 1: next slot of e's other part (toff[e] + supA[e])
+  int2 *pairs;          // MODE 1
+  int64_t entries;      // MODE 1: size of pairs (writes beyond it are dropped)
+  int *err;             // MODE 1: set to TRUSS_ECHECK if a list would overflow
+};
+
+// First e in [0, m] with wpre[e] >= x.
+__device__ __forceinline__ int64_t lower_bound64(const int64_t *a, int64_t m, int64_t x) {
+  int64_t lo = 0, hi = m;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(&a[mid]) < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Out-list of u as seen by one warp: staged in shared memory or read from
+// global memory.  Membership is a branch-free lower bound with a fixed number
+// of halving steps (floor(log2 d) + 1), so all lanes of a warp stay in step.
+struct OutList {
+  const int32_t *L;
+  int d, top;  // top = largest power of two <= d
+  bool staged;
+
+  __device__ __forceinline__ int at(int i) const { return staged ? L[i] : __ldg(&L[i]); }
+
+  // Position of w in out(u), or -1.
+  __device__ __forceinline__ int find(int w) const {
+    int q = 0;  // number of entries < w found so far
+    for (int step = top; step > 0; step >>= 1) {
+      const int nq = q + step;
+      if (nq <= d && at(nq - 1) < w) q = nq;
+    }
+    return (q < d && at(q) == w) ? q : -1;
+  }
+};
+
+// Walk edges (u, L[i]) for i in [i0, i1) (i1 <= d-1).  C = owner counters
+// (MODE 0, int32) or owner cursors (MODE 1, int64), bu = offp[u].
+template <int MODE>
+__device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList &ol, void *Cv,
+                                     int i0, int i1) {
+  const int lane = lane_id();
+  for (int c0 = i0; c0 < i1; c0 += 32) {
+    const int i = c0 + lane;
+    const bool valid = i < i1;
+    const int v = valid ? ol.at(i) : 0;
+    const int64_t vb = valid ? __ldg(&a.offp[v]) : 0;
+    const int len = valid ? (int)(__ldg(&a.offp[v + 1]) - vb) : 0;
+    const int P = warp_incl_scan(len);
+    const int total = __shfl_sync(TR_FULL, P, 31);
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      const int o = warp_owner(P, t < total ? t : total - 1);
+      const int64_t ob = __shfl_sync(TR_FULL, vb, o);
+      const int oP = __shfl_sync(TR_FULL, P, o);
+      const int olen = __shfl_sync(TR_FULL, len, o);
+      if (t < total) {
+        const int64_t evw = ob + (t - (oP - olen));
+        const int w = __ldg(&a.adjp[evw]);
+        const int io = c0 + o;
+        const int q = ol.find(w);
+        if (q >= 0) {
+          if (MODE == 0) {
+            int32_t *C = (int32_t *)Cv;
+            atomicAdd(&a.supB[evw], 1);
+            atomicAdd(&C[q], 1);
+            atomicAdd(&C[io], 1);
+          } else {
+            unsigned long long *C = (unsigned long long *)Cv;
+            const int64_t euv = bu + io, euw = bu + q;
+            const int64_t x1 = (int64_t)atomicAdd(&C[io], 1ull);
+            const int64_t x2 = (int64_t)atomicAdd(&C[q], 1ull);
+            const int64_t x3 = (int64_t)atomicAdd(&a.curB[evw], 1ull);
+            if (x1 < a.entries && x2 < a.entries && x3 < a.entries) {
+              a.pairs[x1] = make_int2((int)euw, (int)evw);
+              a.pairs[x2] = make_int2((int)euv, (int)evw);
+              a.pairs[x3] = make_int2((int)euv, (int)euw);
+            } else {
+              atomicExch(a.err, TRUSS_ECHECK);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// Warps take equal-cost ranges of oriented edges round-robin.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_support(SupArgs a) {
+  constexpr int CAP = Cap<MODE>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  unsigned char *base = smem_raw + (size_t)warp * warp_smem<MODE>();
+  // layout: counters/cursors (8-byte aligned first), then L
+  void *Cs = base;
+  int32_t *Ls = (int32_t *)(base + (size_t)CAP * (MODE == 0 ? 4 : 8));
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = gw; r < a.P; r += nw) {
+    const int64_t ea = lower_bound64(a.wpre, a.m, a.W * r / a.P);
+    const int64_t eb = lower_bound64(a.wpre, a.m, a.W * (r + 1) / a.P);
+    int64_t e = ea;
+    while (e < eb) {
+      const int u = __ldg(&a.esrc[e]);
+      const int64_t bu = __ldg(&a.offp[u]);
+      const int d = (int)(__ldg(&a.offp[u + 1]) - bu);
+      const int i0 = (int)(e - bu);
+      const int iend = (int)(min(eb, bu + d) - bu);
+      e = bu + iend;
+      const int i1 = min(iend, d - 1);  // the last out-neighbour closes no triangle here
+      if (i0 >= i1) continue;
+      const bool whole = i0 == 0 && iend >= d - 1;  // this warp walks all of out(u)
+      OutList ol;
+      ol.d = d;
+      ol.top = 1 << (31 - __clz(d));
+      ol.staged = d <= CAP;
+      void *C;
+      if (ol.staged) {
+        for (int q = lane; q < d; q += 32) {
+          Ls[q] = __ldg(&a.adjp[bu + q]);
+          if (MODE == 0) ((int32_t *)Cs)[q] = 0;
+          else ((unsigned long long *)Cs)[q] = (unsigned long long)__ldg(&a.curA[bu + q]);
+        }
+        __syncwarp();
+        ol.L = Ls;
+        C = Cs;
+        if (MODE == 1 && !whole) C = a.curA + bu;  // cursors shared by several ranges
+      } else {
+        ol.L = a.adjp + bu;
+        C = MODE == 0 ? (void *)(a.supA + bu) : (void *)(a.curA + bu);
+      }
+      walk<MODE>(a, bu, ol, C, i0, i1);
+      __syncwarp();
+      if (MODE == 0 && ol.staged) {
+        const int32_t *Ci = (const int32_t *)Cs;
+        for (int q = lane; q < d; q += 32) {
+          if (whole) a.supA[bu + q] = Ci[q];
+          else if (Ci[q] != 0) atomicAdd(&a.supA[bu + q], Ci[q]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Walk cost of each oriented edge: |out(v)| for (u, v) unless v is the last
+// entry of out(u).
+__global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
+                            const int32_t *esrc, int64_t *cost) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = 0;
+    if (e < m) {
+      const int u = esrc[e];
+      if (e != offp[u + 1] - 1) {
+        const int v = adjp[e];
+        c = offp[v + 1] - offp[v];
+      }
+    }
+    cost[e] = c;
+  }
+}
+
+__global__ void k_sum(int64_t m, const int32_t *supA, const int32_t *supB, int32_t *sup,
+                      int64_t *sup64) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < m) {
+      int32_t s = supA[e] + supB[e];
+      sup[e] = s;
+      sup64[e] = s;
+    } else {
+      sup64[e] = 0;
+    }
+  }
+}
+
+// List cursors: e's owner part starts at toff[e], its other part at
+// toff[e] + supA[e].
+__global__ void k_cursors(int64_t m, const int64_t *toff, const int32_t *supA,
+                          unsigned long long *curA, unsigned long long *curB) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    curA[e] = (unsigned long long)toff[e];
+    curB[e] = (unsigned long long)(toff[e] + supA[e]);
+  }
+}
+
+int launch_walk(int mode, SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
+  int dev = 0, sms = cfg.sms;
+  TR_CUDA(cudaGetDevice(&dev));
+  if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t smem = (size_t)(kBlock / 32) * (mode == 0 ? warp_smem<0>() : warp_smem<1>());
+  int occ = 0;
+  if (mode == 0) {
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_support<0>, kBlock, smem));
+  } else {
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_support<1>, kBlock, smem));
+  }
+  if (occ < 1) occ = 1;
+  const int grid = sms * occ;
+  const int64_t warps = (int64_t)grid * (kBlock / 32);
+  int64_t P = a.W / kRangeWork;
+  if (P < warps) P = warps;
+  if (P > a.m) P = a.m > 0 ? a.m : 1;
+  a.P = P;
+  if (mode == 0) k_support<0><<<grid, kBlock, smem, s>>>(a);
+  else k_support<1><<<grid, kBlock, smem, s>>>(a);
+  TR_LAUNCHED();
+  return TRUSS_OK;
+}
+
+}  // namespace
+
+int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, cudaStream_t s) {
+  const int64_t m = g.m;
+  int32_t *supA = A.get<int32_t>(m), *supB = A.get<int32_t>(m), *sup = A.get<int32_t>(m);
+  int64_t *sup64 = A.get<int64_t>(m + 1), *toff = A.get<int64_t>(m + 1);
+  int64_t *wcost = A.get<int64_t>(m + 1), *wpre = A.get<int64_t>(m + 1);
+  if (!supA || !supB || !sup || !sup64 || !toff || !wcost || !wpre) return TRUSS_ENOMEM;
+  TR_CUDA(cudaMemsetAsync(supA, 0, sizeof(int32_t) * m, s));
+  TR_CUDA(cudaMemsetAsync(supB, 0, sizeof(int32_t) * m, s));
+  int64_t W = 0;
+  if (m > 0) {
+    k_walk_cost<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, g.offp, g.adjp, g.esrc, wcost);
+    TR_LAUNCHED();
+    size_t tb = 0;
+    TR_TRY(exclusive_sum_i64(nullptr, &tb, wcost, wpre, m + 1, s));
+    void *tmp = A.alloc(tb);
+    if (!tmp) return TRUSS_ENOMEM;
+    TR_TRY(exclusive_sum_i64(tmp, &tb, wcost, wpre, m + 1, s));
+    TR_CUDA(cudaMemcpyAsync(&W, wpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaStreamSynchronize(s));
+  }
+  if (W > 0) {
+    SupArgs a{};
+    a.n = g.n;
+    a.m = m;
+    a.offp = g.offp;
+    a.adjp = g.adjp;
+    a.esrc = g.esrc;
+    a.wpre = wpre;
+    a.W = W;
+    a.supA = supA;
+    a.supB = supB;
+    TR_TRY(launch_walk(0, a, cfg, s));
+  }
+  k_sum<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, supA, supB, sup, sup64);
+  TR_LAUNCHED();
+  size_t tb = 0;
+  TR_TRY(exclusive_sum_i64(nullptr, &tb, sup64, toff, m + 1, s));
+  void *tmp = A.alloc(tb);
+  if (!tmp) return TRUSS_ENOMEM;
+  TR_TRY(exclusive_sum_i64(tmp, &tb, sup64, toff, m + 1, s));
+  int64_t total = 0;
+  TR_CUDA(cudaMemcpyAsync(&total, toff + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TR_CUDA(cudaStreamSynchronize(s));
+  out->sup = sup;
+  out->supA = supA;
+  out->toff = toff;
+  out->wpre = wpre;
+  out->walk = W;
+  out->entries = total;
+  return TRUSS_OK;
+}
+
+int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &so, int2 *pairs,
+              cudaStream_t s) {
+  const int64_t m = g.m;
+  if (m == 0 || so.entries == 0) return TRUSS_OK;
+  unsigned long long *curA = A.get<unsigned long long>(m), *curB = A.get<unsigned long long>(m);
+  int *err = A.get<int>(1);
+  if (!curA || !curB || !err) return TRUSS_ENOMEM;
+  TR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  k_cursors<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.supA, curA, curB);
+  TR_LAUNCHED();
+  SupArgs a{};
+  a.n = g.n;
+  a.m = m;
+  a.offp = g.offp;
+  a.adjp = g.adjp;
+  a.esrc = g.esrc;
+  a.wpre = so.wpre;
+  a.W = so.walk;
+  a.supA = so.supA;
+  a.curA = curA;
+  a.curB = curB;
+  a.pairs = pairs;
+  a.entries = so.entries;
+  a.err = err;
+  TR_TRY(launch_walk(1, a, cfg, s));
+  int h_err = 0;
+  TR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TR_CUDA(cudaStreamSynchronize(s));
+  return h_err != 0 ? TRUSS_ECHECK : TRUSS_OK;
+}
+
+}  // namespace tr
+
+namespace tr {
+
+namespace {
+// Bytes the support walk must move, independent of caching: per owner u with
+// d = |out(u)| >= 2, its two offsets (16 B), out(u) read (4d) and the owner
+// counts stored (4d); per walked edge (u, v) (all but the last of out(u)),
+// v's two offsets (16 B) and out(v) (4 |out(v)|).
+__global__ void k_count_walk(int64_t n, const int64_t *offp, const int32_t *adjp,
+                             unsigned long long *acc) {
+  unsigned long long local = 0;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bu = offp[u], d = offp[u + 1] - bu;
+    if (d < 2) continue;
+    local += 16ull + 8ull * (unsigned long long)d;
+    for (int64_t i = 0; i < d - 1; i++) {
+      const int v = adjp[bu + i];
+      local += 16ull + 4ull * (unsigned long long)(offp[v + 1] - offp[v]);
+    }
+  }
+  for (int o = 16; o >= 1; o >>= 1) local += __shfl_down_sync(TR_FULL, local, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(acc, local);
+}
+}  // namespace
+
+// Algorithmic bytes of the support pass: walk bytes + 8 B per triangle (the
+// read-modify-write of supB).  Of the list pass: walk bytes + 60 B per
+// triangle (three 8-B list entries written, three 8-B list offsets and one
+// 4-B owner count read, one 8-B cursor read-modify-write).
+int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, double *b_sup,
+                        double *b_lists, cudaStream_t s) {
+  unsigned long long *acc = A.get<unsigned long long>(1);
+  if (!acc) return TRUSS_ENOMEM;
+  TR_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
+  if (g.n > 0 && g.m > 0) {
+    k_count_walk<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, g.offp, g.adjp, acc);
+    TR_LAUNCHED();
+  }
+  unsigned long long h = 0;
+  TR_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  TR_CUDA(cudaStreamSynchronize(s));
+  *b_sup = (double)h + 8.0 * (double)triangles;
+  *b_lists = (double)h + 60.0 * (double)triangles;
+  return TRUSS_OK;
+}
+
+}  // namespace tr

@@ -1,0 +1,234 @@
+"""ctypes binding of ``include/truss.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+computation of its own: buffers (torch tensors, on the GPU or the CPU, or numpy
+arrays) are passed to the CUDA library by pointer.  The library must be built
+(``__graft_entry__.build()`` or ``python -m paper_1205_6693_gb300._build``);
+if it is missing this module raises instead of computing anything elsewhere.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+TRUSS_OK = 0
+TRUSS_EINVAL = -1
+TRUSS_ENOMEM = -2
+TRUSS_ECUDA = -3
+TRUSS_ETIMEOUT = -4
+TRUSS_EAGAIN = -5
+TRUSS_EBUSY = -6
+TRUSS_ESHUTDOWN = -7
+TRUSS_ECHECK = -8
+
+ERRORS = {TRUSS_EINVAL: "EINVAL", TRUSS_ENOMEM: "ENOMEM", TRUSS_ECUDA: "ECUDA",
+          TRUSS_ETIMEOUT: "ETIMEOUT", TRUSS_EAGAIN: "EAGAIN", TRUSS_EBUSY: "EBUSY",
+          TRUSS_ESHUTDOWN: "ESHUTDOWN", TRUSS_ECHECK: "ECHECK"}
+
+
+class TrussError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib().truss_strerror(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})")
+
+
+class truss_opts(ctypes.Structure):
+    _fields_ = [("wait_limit_ns", ctypes.c_int64), ("profile", ctypes.c_int32),
+                ("count_bytes", ctypes.c_int32), ("support_block", ctypes.c_int32),
+                ("peel_blocks_per_sm", ctypes.c_int32), ("peel_small_frontier", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class truss_run_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("rows", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("triangles", ctypes.c_int64), ("kmax", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("subrounds", ctypes.c_int32),
+                ("graphs", ctypes.c_int32), ("ms_build", ctypes.c_float),
+                ("ms_support", ctypes.c_float), ("ms_lists", ctypes.c_float),
+                ("ms_peel", ctypes.c_float), ("ms_scatter", ctypes.c_float),
+                ("ms_total", ctypes.c_float), ("bytes_support", ctypes.c_double),
+                ("bytes_lists", ctypes.c_double), ("bytes_peel", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+# Symbols declared in include/truss.h (checked by the CPU test suite).
+EXPORTS = ("truss_strerror", "truss_ctx_create", "truss_ctx_destroy", "truss_support",
+           "truss_decompose", "truss_decompose_batch", "truss_last_stats")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if _build.stale():
+            try:
+                _build.build()
+            except Exception as e:  # noqa: BLE001 - re-raised with context
+                raise RuntimeError(f"libtruss.so is missing or stale and could not be built: {e}")
+        L = ctypes.CDLL(_build.LIB)
+        L.truss_strerror.restype = ctypes.c_char_p
+        L.truss_strerror.argtypes = [ctypes.c_int]
+        L.truss_ctx_create.restype = ctypes.c_int
+        L.truss_ctx_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int,
+                                       ctypes.POINTER(truss_opts)]
+        L.truss_ctx_destroy.restype = ctypes.c_int
+        L.truss_ctx_destroy.argtypes = [_vp]
+        L.truss_support.restype = ctypes.c_int
+        L.truss_support.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp]
+        L.truss_decompose.restype = ctypes.c_int
+        L.truss_decompose.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.truss_decompose_batch.restype = ctypes.c_int
+        L.truss_decompose_batch.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.truss_last_stats.restype = ctypes.c_int
+        L.truss_last_stats.argtypes = [_vp, ctypes.POINTER(truss_run_stats)]
+        _LIB = L
+    return _LIB
+
+
+def load():
+    """Load (building if needed) the CUDA library; returns the ctypes handle."""
+    return _lib()
+
+
+# ------------------------------------------------------------ marshalling ---
+def _ptr(x, dtype=np.int32):
+    """Device or host address of a torch tensor / numpy array (or None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags.c_contiguous:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype).name} array")
+        return x.ctypes.data
+    # torch tensor
+    import torch
+    want = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+    if x.dtype != want or not x.is_contiguous():
+        raise TypeError(f"expected a contiguous {want} tensor")
+    return x.data_ptr()
+
+
+def _stream(stream, *tensors):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    for t in tensors:
+        if t is not None and not isinstance(t, np.ndarray) and t.is_cuda:
+            import torch
+            return torch.cuda.current_stream(t.device).cuda_stream
+    return None
+
+
+def _check(rc, where):
+    if rc != TRUSS_OK:
+        raise TrussError(rc, where)
+
+
+def _len(x):
+    return int(x.shape[0])
+
+
+# ----------------------------------------------------------- entry points ---
+def truss_strerror(code: int) -> str:
+    return _lib().truss_strerror(code).decode()
+
+
+def truss_ctx_create(device: int = 0, opts: truss_opts | None = None):
+    ctx = _vp()
+    _check(_lib().truss_ctx_create(ctypes.byref(ctx), device,
+                                   ctypes.byref(opts) if opts is not None else None),
+           "truss_ctx_create")
+    return ctx
+
+
+def truss_ctx_destroy(ctx) -> None:
+    _check(_lib().truss_ctx_destroy(ctx), "truss_ctx_destroy")
+
+
+def truss_support(ctx, n: int, src, dst, support_out, stream=None) -> None:
+    rows = _len(src)
+    _check(_lib().truss_support(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(support_out),
+                                _stream(stream, src, support_out)), "truss_support")
+
+
+def truss_decompose(ctx, n: int, src, dst, support_out, truss_out, kmax_out=None,
+                    stream=None) -> int:
+    """Returns k_max (also written to kmax_out when given)."""
+    rows = _len(src)
+    k = np.zeros(1, np.int32)
+    kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
+    _check(_lib().truss_decompose(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(support_out),
+                                  _ptr(truss_out), kp, _stream(stream, src, truss_out)),
+           "truss_decompose")
+    return int(k[0]) if kmax_out is None else -1
+
+
+def truss_decompose_batch(ctx, n, row_off, src, dst, support_out, truss_out, kmax_out=None,
+                          stream=None) -> None:
+    """n and row_off are host int64 arrays (G and G+1 entries)."""
+    n = np.ascontiguousarray(n, np.int64)
+    row_off = np.ascontiguousarray(row_off, np.int64)
+    G = len(n)
+    _check(_lib().truss_decompose_batch(ctx, G, n.ctypes.data, row_off.ctypes.data, _ptr(src),
+                                        _ptr(dst), _ptr(support_out), _ptr(truss_out),
+                                        _ptr(kmax_out), _stream(stream, src, truss_out)),
+           "truss_decompose_batch")
+
+
+def truss_last_stats(ctx) -> dict:
+    st = truss_run_stats()
+    _check(_lib().truss_last_stats(ctx, ctypes.byref(st)), "truss_last_stats")
+    return st.as_dict()
+
+
+class Context:
+    """Owns a truss_ctx; the methods are the entry points above."""
+
+    def __init__(self, device: int = 0, profile: bool = False, count_bytes: bool = False,
+                 wait_limit_ns: int = 0, **kw):
+        o = truss_opts()
+        o.profile = int(profile)
+        o.count_bytes = int(count_bytes)
+        o.wait_limit_ns = int(wait_limit_ns)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        self.ctx = truss_ctx_create(device, o)
+
+    def close(self):
+        if self.ctx is not None:
+            truss_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def support(self, n, src, dst, support_out, stream=None):
+        return truss_support(self.ctx, n, src, dst, support_out, stream)
+
+    def decompose(self, n, src, dst, support_out, truss_out, kmax_out=None, stream=None):
+        return truss_decompose(self.ctx, n, src, dst, support_out, truss_out, kmax_out, stream)
+
+    def decompose_batch(self, n, row_off, src, dst, support_out, truss_out, kmax_out=None,
+                        stream=None):
+        return truss_decompose_batch(self.ctx, n, row_off, src, dst, support_out, truss_out,
+                                     kmax_out, stream)
+
+    def stats(self):
+        return truss_last_stats(self.ctx)

@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle,
+element by element and bit-exact (all outputs are integers)."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1205_6693_gb300 import truss as T
+    c = T.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_run(ctx, n, src, dst, host=False, support_only=False):
+    if host:
+        s, d = np.ascontiguousarray(src, np.int32), np.ascontiguousarray(dst, np.int32)
+        sup = np.empty(len(s), np.int32)
+        tr = np.empty(len(s), np.int32)
+    else:
+        dev = torch.device("cuda:0")
+        s = torch.from_numpy(np.ascontiguousarray(src, np.int32)).to(dev)
+        d = torch.from_numpy(np.ascontiguousarray(dst, np.int32)).to(dev)
+        sup = torch.empty_like(s)
+        tr = torch.empty_like(s)
+    if support_only:
+        ctx.support(n, s, d, sup)
+        kmax = None
+    else:
+        kmax = ctx.decompose(n, s, d, sup, tr)
+    torch.cuda.synchronize()
+    if host:
+        return sup, tr, kmax
+    return sup.cpu().numpy(), tr.cpu().numpy(), kmax
+
+
+def assert_same(ctx, n, src, dst, **kw):
+    ref = oracle.truss(n, src, dst)
+    sup, tr, kmax = gpu_run(ctx, n, src, dst, **kw)
+    bad_s = np.nonzero(sup != ref.support)[0]
+    bad_t = np.nonzero(tr != ref.truss)[0]
+    assert len(bad_s) == 0, f"support differs on {len(bad_s)} rows, first {bad_s[:5]}"
+    assert len(bad_t) == 0, f"truss differs on {len(bad_t)} rows, first {bad_t[:5]}"
+    assert kmax == ref.kmax
+    st = ctx.stats()
+    assert st["m"] == ref.m and st["triangles"] == ref.triangles
+    return ref
+
+
+# ------------------------------------------------------------- fixtures ---
+def test_fig2_example(ctx):
+    from test_oracle import fig2
+    classes = fig2()
+    edges = sorted(classes)
+    src = np.array([a for a, _ in edges], np.int32)
+    dst = np.array([b for _, b in edges], np.int32)
+    _, tr, kmax = gpu_run(ctx, 12, src, dst)
+    assert [int(t) for t in tr] == [classes[e] for e in edges]
+    assert kmax == 5
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 12, 33, 64])
+def test_complete_graphs(ctx, n):
+    a, b = np.triu_indices(n, 1)
+    sup, tr, kmax = gpu_run(ctx, n, a.astype(np.int32), b.astype(np.int32))
+    assert (sup == n - 2).all() and (tr == n).all() and kmax == n
+
+
+# ---------------------------------------------------- seeded random graphs ---
+@pytest.mark.parametrize("seed", range(8))
+def test_er_with_cliques(ctx, seed):
+    n = 200 + 700 * seed
+    src, dst = graphgen.er(n, 6 * n, seed=seed)
+    perm = graphgen.permutation(n, seed=seed, stream=1)
+    sizes = [5 + seed, 9 + 2 * seed, 30]
+    src, dst = graphgen.add_cliques(src, dst, perm[: sum(sizes)], sizes)
+    assert_same(ctx, n, src, dst)
+
+
+@pytest.mark.parametrize("scale,ef", [(8, 8), (10, 16), (12, 16), (14, 8), (15, 16)])
+def test_rmat_raw_rows(ctx, scale, ef):
+    # raw R-MAT rows keep duplicates, reversed pairs and self-loops
+    n, (src, dst) = 2 ** scale, graphgen.rmat_raw(scale, ef * 2 ** scale, seed=scale)
+    assert_same(ctx, n, src, dst)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_chung_lu_small(ctx, seed):
+    n = 20000
+    src, dst = graphgen.chung_lu(n, 200000, 20.0, 2000.0, 2.1, seed=seed)
+    assert_same(ctx, n, src, dst)
+
+
+def test_tiny_config(ctx):
+    n, src, dst = graphgen.tiny()
+    ref = assert_same(ctx, n, src, dst)
+    assert ref.kmax == 32
+
+
+def test_host_pointers_match_device(ctx):
+    n, src, dst = graphgen.tiny()
+    ref = oracle.truss(n, src, dst)
+    sup, tr, kmax = gpu_run(ctx, n, src, dst, host=True)
+    assert np.array_equal(sup, ref.support) and np.array_equal(tr, ref.truss)
+    assert kmax == ref.kmax
+
+
+def test_support_only(ctx):
+    n, (src, dst) = 4096, graphgen.rmat_raw(12, 16 * 4096, seed=5)
+    ref = oracle.truss(n, src, dst, with_truss=False)
+    sup, _, _ = gpu_run(ctx, n, src, dst, support_only=True)
+    assert np.array_equal(sup, ref.support)
+
+
+def test_deterministic(ctx):
+    n, (src, dst) = 2 ** 13, graphgen.rmat_raw(13, 16 * 2 ** 13, seed=3)
+    a = gpu_run(ctx, n, src, dst)
+    b = gpu_run(ctx, n, src, dst)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ------------------------------------------------------------ edge cases ---
+def test_empty_graph(ctx):
+    e = np.zeros(0, np.int32)
+    sup, tr, kmax = gpu_run(ctx, 10, e, e)
+    assert len(sup) == 0 and kmax == 0
+
+
+def test_only_self_loops(ctx):
+    x = np.arange(5, dtype=np.int32)
+    sup, tr, kmax = gpu_run(ctx, 5, x, x)
+    assert (sup == -1).all() and (tr == -1).all() and kmax == 0
+
+
+def test_single_edge_and_duplicates(ctx):
+    src = np.array([0, 1, 0, 2, 2], np.int32)
+    dst = np.array([1, 0, 1, 2, 0], np.int32)
+    assert_same(ctx, 3, src, dst)
+
+
+def test_isolated_vertices_and_large_n(ctx):
+    n = 5_000_000
+    src = np.array([4_999_999, 17, 17, 123456], np.int32)
+    dst = np.array([17, 123456, 4_999_999, 4_999_999], np.int32)
+    ref = assert_same(ctx, n, src, dst)
+    assert ref.kmax == 3  # the three distinct edges form one triangle
+
+
+def test_invalid_ids_rejected(ctx):
+    from paper_1205_6693_gb300.truss import TRUSS_EINVAL, TrussError
+    for bad in ([0, 5], [-1, 2]):
+        src = np.array([0, bad[0]], np.int32)
+        dst = np.array([1, bad[1]], np.int32)
+        with pytest.raises(TrussError) as ei:
+            gpu_run(ctx, 5, src, dst)
+        assert ei.value.code == TRUSS_EINVAL
+    # the context stays usable
+    assert_same(ctx, 3, np.array([0, 1, 2], np.int32), np.array([1, 2, 0], np.int32))
+
+
+# ------------------------------------------------------------------ batch ---
+def test_batch_matches_oracle_per_graph(ctx):
+    G = 300
+    ns, off, src, dst = graphgen.batch(G)
+    dev = torch.device("cuda:0")
+    s = torch.from_numpy(src).to(dev)
+    d = torch.from_numpy(dst).to(dev)
+    sup = torch.empty_like(s)
+    tr = torch.empty_like(s)
+    kmax = torch.empty(G, dtype=torch.int32, device=dev)
+    ctx.decompose_batch(ns, off, s, d, sup, tr, kmax)
+    torch.cuda.synchronize()
+    sup, tr, kmax = sup.cpu().numpy(), tr.cpu().numpy(), kmax.cpu().numpy()
+    for g in range(G):
+        a, b = off[g], off[g + 1]
+        ref = oracle.truss(int(ns[g]), src[a:b], dst[a:b])
+        assert np.array_equal(sup[a:b], ref.support), g
+        assert np.array_equal(tr[a:b], ref.truss), g
+        assert kmax[g] == ref.kmax, g
+
+
+# ------------------------------------------------------------- full size ---
+def _digest(name):
+    with open(os.path.join(GOLDEN, "digests.json")) as f:
+        return json.load(f)[name]
+
+
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
+
+
+def _check_full(ctx, name, gen):
+    exp = _digest(name)
+    n, src, dst = gen()
+    sup, tr, kmax = gpu_run(ctx, n, src, dst)
+    idx = np.array(exp["sample_rows"], np.int64)
+    assert np.array_equal(sup[idx], np.array(exp["sample_support"], np.int32))
+    assert np.array_equal(tr[idx], np.array(exp["sample_truss"], np.int32))
+    st = ctx.stats()
+    assert st["m"] == exp["m"] and st["triangles"] == exp["triangles"]
+    assert kmax == exp["kmax"]
+    assert _sha(sup) == exp["sha256_support"]
+    assert _sha(tr) == exp["sha256_truss"]
+
+
+def test_mid_full_size(ctx):
+    _check_full(ctx, "mid", graphgen.mid)
+
+
+def test_large_full_size(ctx):
+    if "large" not in json.load(open(os.path.join(GOLDEN, "digests.json"))):
+        pytest.skip("no stored oracle digest for the large workload")
+    _check_full(ctx, "large", graphgen.large)
