@@ -9,9 +9,11 @@
 // sub-rounds: all alive edges whose residual support res is <= k-2 form the
 // frontier F and are removed together.
 //
-//  scan (per level k):  F = {alive e : res[e] <= k-2}; the other alive edges
-//        are compacted into the next alive list and their minimum residual
-//        is taken, so an empty level jumps straight to k = min res + 2.
+//  scan (per level k):  F = {alive e : res[e] <= k-2}; the minimum residual
+//        of the other alive edges is taken, so an empty level jumps straight
+//        to k = min res + 2.  The list of alive edges scanned is rewritten
+//        without the removed ones only when at most half of it is still
+//        alive.
 //  sub-round:  for every e in F and every triangle {e, e1, e2} on e's list
 //        whose edges are all still alive, the triangle is charged exactly
 //        once, by the lowest-id edge among those of its edges that are in F:
@@ -21,10 +23,16 @@
 //
 // Load balance inside a sub-round (its time is that of the slowest warp):
 // when an edge joins a frontier it is expanded into work items of kItem list
-// entries each (at least one item, which also records its truss number), and
-// every warp takes 4 items per iteration, 8 lanes per item.  A warp's share of
-// a sub-round is then at most ceil(items / (4 * warps)) iterations, whatever
-// the lengths of the lists.
+// entries each (at least one item, which also records its truss number); an
+// item carries its edge, its entry count and the offset of its entries, so a
+// warp goes from the item straight to the list.  Every warp takes 4 items per
+// iteration, 8 lanes per item and 2 entries per lane (independent loads in
+// flight).  A warp's share of a sub-round is then at most
+// ceil(items / (4 * warps)) iterations, whatever the lengths of the lists.
+// Appends are staged per warp in shared memory and flushed with one atomic
+// reservation per buffer, and per-level reductions (minimum residual, alive
+// count) are combined per block first: a single global counter hit by every
+// warp would serialise the whole grid on one L2 address.
 // The queues use monotonically increasing 64-bit counters (never reset).  The
 // block that completes a grid barrier copies them into a snapshot slot of
 // that barrier's generation before releasing it, and every block takes its
@@ -52,7 +60,10 @@ namespace tr {
 namespace {
 
 constexpr int kPeelBlock = 512;
-constexpr int kItem = 8;  // list entries per work item (one lane each)
+constexpr int kWarps = kPeelBlock / 32;
+constexpr int kItem = 16;  // list entries per work item (8 lanes x 2)
+constexpr int kWQ = 64;    // work items staged per warp
+constexpr int kWA = 128;   // alive-list entries staged per warp
 
 struct PeelCtl {
   unsigned bar_count;
@@ -61,8 +72,8 @@ struct PeelCtl {
   int pad0;
   unsigned long long qf;  // frontier items appended so far (F and N alternate)
   unsigned long long qa;  // alive-list entries appended so far
-  int minres[3];          // per scan phase (slot = scan index % 3)
-  int pad1;
+  int minres[3];          // per scan (slot = scan index % 3)
+  int live[3];            // alive edges left after each scan
   unsigned long long snap[2][2];  // qf, qa at the last two barriers
   int levels, subrounds, kmax, pad2;
   unsigned long long entries, decrements, scanned;
@@ -77,7 +88,7 @@ struct PeelArgs {
   int32_t *stamp;
   int32_t *truss;
   int32_t *alive0, *alive1;
-  int2 *Q0, *Q1;      // frontier work items (edge, item index)
+  int4 *Q0, *Q1;      // frontier work items (edge, count | first << 8, offset lo, hi)
   int64_t item_cap;   // capacity of Q0 and Q1
   int4 *trace;        // optional: per sub-round (k, items, 0, 0)
   int trace_cap;
@@ -128,91 +139,194 @@ __device__ bool grid_barrier(PeelCtl *c, long long wait_ns, unsigned long long *
 
 __device__ __forceinline__ int items_of(int len) { return len > 0 ? (len + kItem - 1) / kItem : 1; }
 
-// Append the work items of edge p (for each lane with `push`) to queue Q,
-// stamping p with `stamp_val`.  All lanes call it.
-__device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, int2 *Q,
-                                           unsigned long long base_q, int stamp_val) {
+// Per-warp staging buffers in shared memory (counts are warp-uniform).
+struct WarpBuf {
+  int4 *items;
+  int ni;
+  int32_t *alive;
+  int na;
+};
+
+// Write the staged items to queue Q with one reservation.
+__device__ __forceinline__ void flush_items(const PeelArgs &a, WarpBuf &wb, int4 *Q,
+                                            unsigned long long base_q) {
+  if (wb.ni == 0) return;
   const int lane = lane_id();
-  int n = 0;
+  unsigned long long b = 0;
+  if (lane == 0) b = atomicAdd(&a.ctl->qf, (unsigned long long)wb.ni);
+  const long long b0 = (long long)(__shfl_sync(TR_FULL, b, 0) - base_q);
+  for (int t = lane; t < wb.ni; t += 32)
+    if (b0 + t < a.item_cap) Q[b0 + t] = wb.items[t];
+  __syncwarp();
+  wb.ni = 0;
+}
+
+__device__ __forceinline__ void flush_alive(const PeelArgs &a, WarpBuf &wb, int32_t *A2,
+                                            unsigned long long base_a) {
+  if (wb.na == 0) return;
+  const int lane = lane_id();
+  unsigned long long b = 0;
+  if (lane == 0) b = atomicAdd(&a.ctl->qa, (unsigned long long)wb.na);
+  const long long b0 = (long long)(__shfl_sync(TR_FULL, b, 0) - base_a);
+  for (int t = lane; t < wb.na; t += 32)
+    if (b0 + t < a.m) A2[b0 + t] = wb.alive[t];
+  __syncwarp();
+  wb.na = 0;
+}
+
+// Queue the alive edges of the lanes with `keep` for the rewritten list.
+__device__ __forceinline__ void push_alive(const PeelArgs &a, bool keep, int e, WarpBuf &wb,
+                                           int32_t *A2, unsigned long long base_a) {
+  const unsigned mask = __ballot_sync(TR_FULL, keep);
+  if (mask == 0) return;
+  const int tot = __popc(mask);
+  if (wb.na + tot > kWA) flush_alive(a, wb, A2, base_a);
+  if (keep) wb.alive[wb.na + __popc(mask & ((1u << lane_id()) - 1u))] = e;
+  __syncwarp();
+  wb.na += tot;
+}
+
+// Append the work items of edge p (for each lane with `push`) to queue Q,
+// stamping p with `stamp_val`.  All lanes call it.  Small batches go through
+// the warp's staging buffer; a batch larger than the buffer is written
+// straight to Q with its own reservation.
+__device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, WarpBuf &wb,
+                                           int4 *Q, unsigned long long base_q, int stamp_val) {
+  const int lane = lane_id();
+  int n = 0, L = 0;
+  int64_t lb = 0;
   if (push) {
-    n = items_of(__ldg(&a.sup[p]));
+    L = __ldg(&a.sup[p]);
+    lb = __ldg(&a.toff[p]);
+    n = items_of(L);
     a.stamp[p] = stamp_val;
   }
   const int P = warp_incl_scan(n);
   const int tot = __shfl_sync(TR_FULL, P, 31);
   if (tot == 0) return;
-  unsigned long long b = 0;
-  if (lane == 31) b = atomicAdd(&a.ctl->qf, (unsigned long long)tot);
-  const long long b0 = (long long)(__shfl_sync(TR_FULL, b, 31) - base_q);
+  int4 *dst;
+  long long b0;
+  if (tot > kWQ) {
+    unsigned long long b = 0;
+    if (lane == 31) b = atomicAdd(&a.ctl->qf, (unsigned long long)tot);
+    b0 = (long long)(__shfl_sync(TR_FULL, b, 31) - base_q);
+    dst = Q;
+  } else {
+    if (wb.ni + tot > kWQ) flush_items(a, wb, Q, base_q);
+    b0 = wb.ni;
+    dst = wb.items;
+  }
+  const long long lim = tot > kWQ ? a.item_cap : (long long)kWQ;
   for (int t0 = 0; t0 < tot; t0 += 32) {
     const int t = t0 + lane;
     const int o = warp_owner(P, t < tot ? t : tot - 1);
     const int po = __shfl_sync(TR_FULL, p, o);
     const int Po = __shfl_sync(TR_FULL, P, o);
     const int no = __shfl_sync(TR_FULL, n, o);
+    const int Lo = __shfl_sync(TR_FULL, L, o);
+    const int64_t lbo = __shfl_sync(TR_FULL, lb, o);
     const long long idx = b0 + t;
-    if (t < tot && idx < a.item_cap) Q[idx] = make_int2(po, t - (Po - no));
-  }
-}
-
-// One triangle entry (the partner edges p1, p2 of frontier edge e) in
-// sub-round s at level k; all lanes call it (`valid` masks idle lanes).
-// Charges the triangle by the lowest-id frontier edge among its edges and
-// appends partners whose residual crosses k-1 -> k-2 to the next frontier.
-__device__ __forceinline__ void charge(const PeelArgs &a, bool valid, int e, int2 pr, int k,
-                                       int s, int2 *N, unsigned long long base_f,
-                                       unsigned long long &n_dec) {
-  bool d1 = false, d2 = false;
-  const int p1 = pr.x, p2 = pr.y;
-  if (valid) {
-    if ((uint32_t)p1 >= (uint32_t)a.m || (uint32_t)p2 >= (uint32_t)a.m) {
-      atomicExch(&a.ctl->err, TRUSS_ECHECK);  // corrupt list entry: skip it
-    } else {
-      const int s1 = __ldcg(&a.stamp[p1]), s2 = __ldcg(&a.stamp[p2]);
-      const bool dead1 = s1 > 0 && s1 < s, dead2 = s2 > 0 && s2 < s;
-      if (!dead1 && !dead2) {
-        const bool in1 = s1 == s, in2 = s2 == s;
-        if (!in1 && !in2) {
-          d1 = true;
-          d2 = true;
-        } else if (in1 && !in2) {
-          d2 = e < p1;  // e and e1 in F: the lower id charges e2
-        } else if (!in1 && in2) {
-          d1 = e < p2;
-        }
-      }
+    if (t < tot && idx < lim) {
+      const int it = t - (Po - no);
+      const int start = it * kItem;
+      const int cnt = Lo > 0 ? min(kItem, Lo - start) : 0;
+      const int64_t off = lbo + start;
+      dst[idx] = make_int4(po, cnt | ((it == 0) << 8), (int)(uint32_t)off,
+                           (int)(uint32_t)((uint64_t)off >> 32));
     }
   }
-  bool push1 = false, push2 = false;
-  if (d1) push1 = atomicSub(&a.res[p1], 1) == k - 1;
-  if (d2) push2 = atomicSub(&a.res[p2], 1) == k - 1;
-  n_dec += (unsigned long long)(d1 + d2);
-  if (__any_sync(TR_FULL, push1 || push2)) {
-    push_items(a, push1, p1, N, base_f, s + 1);
-    push_items(a, push2, p2, N, base_f, s + 1);
+  __syncwarp();
+  if (tot <= kWQ) wb.ni += tot;
+}
+
+// Decide whether frontier edge e charges the triangle {e, p1, p2} in
+// sub-round s: all three edges alive, and e the lowest-id frontier edge among
+// them.  d1 / d2 = decrement p1 / p2 (the partners not in the frontier).
+__device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int2 pr, int s,
+                                       bool &d1, bool &d2) {
+  d1 = d2 = false;
+  if (!valid) return;
+  const int p1 = pr.x, p2 = pr.y;
+  if ((uint32_t)p1 >= (uint32_t)a.m || (uint32_t)p2 >= (uint32_t)a.m) {
+    atomicExch(&a.ctl->err, TRUSS_ECHECK);  // corrupt list entry: skip it
+    return;
+  }
+  const int s1 = __ldcg(&a.stamp[p1]), s2 = __ldcg(&a.stamp[p2]);
+  const bool dead1 = s1 > 0 && s1 < s, dead2 = s2 > 0 && s2 < s;
+  if (dead1 || dead2) return;
+  const bool in1 = s1 == s, in2 = s2 == s;
+  if (!in1 && !in2) {
+    d1 = true;
+    d2 = true;
+  } else if (in1 && !in2) {
+    d2 = e < p1;  // e and e1 in F: the lower id charges e2
+  } else if (!in1 && in2) {
+    d1 = e < p2;
   }
 }
 
-__global__ void __launch_bounds__(kPeelBlock) k_peel(PeelArgs a) {
+// Two triangle entries per lane (all lanes call it; `va`/`vb` mask idle
+// entries).  Each charged triangle decrements its partners outside the
+// frontier; a partner whose residual crosses k-1 -> k-2 joins the next
+// frontier.
+__device__ __forceinline__ void charge2(const PeelArgs &a, int e, bool va, int2 pa, bool vb,
+                                        int2 pb, int k, int s, WarpBuf &wb, int4 *N,
+                                        unsigned long long base_f, unsigned long long &n_dec) {
+  bool a1, a2, b1, b2;
+  decide(a, va, e, pa, s, a1, a2);
+  decide(a, vb, e, pb, s, b1, b2);
+  int o1 = INT_MAX, o2 = INT_MAX, o3 = INT_MAX, o4 = INT_MAX;
+  if (a1) o1 = atomicSub(&a.res[pa.x], 1);
+  if (a2) o2 = atomicSub(&a.res[pa.y], 1);
+  if (b1) o3 = atomicSub(&a.res[pb.x], 1);
+  if (b2) o4 = atomicSub(&a.res[pb.y], 1);
+  n_dec += (unsigned long long)(a1 + a2 + b1 + b2);
+  const bool q1 = o1 == k - 1, q2 = o2 == k - 1, q3 = o3 == k - 1, q4 = o4 == k - 1;
+  if (__any_sync(TR_FULL, q1 || q2 || q3 || q4)) {
+    push_items(a, q1, pa.x, wb, N, base_f, s + 1);
+    push_items(a, q2, pa.y, wb, N, base_f, s + 1);
+    push_items(a, q3, pb.x, wb, N, base_f, s + 1);
+    push_items(a, q4, pb.y, wb, N, base_f, s + 1);
+  }
+}
+
+// MINB = resident blocks per SM the register budget is sized for (1: up to
+// 128 registers per thread, 2: 64).
+template <int MINB>
+__global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   const int lane = lane_id();
-  const int nw = blockDim.x >> 5;
-  const int64_t gwarp = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5);
-  const int64_t twarps = (int64_t)gridDim.x * nw;
+  const int wib = threadIdx.x >> 5;
+  const int64_t gwarp = (int64_t)blockIdx.x * kWarps + wib;
+  const int64_t twarps = (int64_t)gridDim.x * kWarps;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   PeelCtl *ctl = a.ctl;
   __shared__ unsigned long long snap[2];  // qf, qa at the last barrier
+  __shared__ int4 s_items[kWarps][kWQ];
+  __shared__ int32_t s_alive[kWarps][kWA];
+  __shared__ int s_minres, s_live;
+  WarpBuf wb{s_items[wib], 0, s_alive[wib], 0};
+  if (threadIdx.x == 0) {
+    s_minres = INT_MAX;
+    s_live = 0;
+  }
+  __syncthreads();
 
   int k = 2, s = 1, sc = 0;
   unsigned long long base_f = 0, base_a = 0;
   int32_t *alive = a.alive0, *alive2 = a.alive1;
-  int2 *F = a.Q0, *N = a.Q1;
+  int4 *F = a.Q0, *N = a.Q1;
   int64_t nAlive = a.m;
+  bool compact = false;  // rewrite the alive list during this scan
   unsigned long long n_entries = 0, n_dec = 0, n_scan = 0;
 
   for (;;) {
     // ------------------------------------------------------------ scan ---
-    int *mres = &ctl->minres[sc % 3];
-    if (leader) ctl->minres[(sc + 1) % 3] = INT_MAX;
+    const int slot = sc % 3;
+    if (leader) {
+      ctl->minres[(sc + 1) % 3] = INT_MAX;
+      ctl->live[(sc + 1) % 3] = 0;
+    }
+    int wmin = INT_MAX, wlive = 0;
     for (int64_t base = gwarp * 32; base < nAlive; base += twarps * 32) {
       const int64_t i = base + lane;
       int e = -1, r = 0;
@@ -226,23 +340,41 @@ __global__ void __launch_bounds__(kPeelBlock) k_peel(PeelArgs a) {
       }
       const bool toF = live && r <= k - 2;
       const bool keep = live && !toF;
-      push_items(a, toF, e, F, base_f, s);
-      const long long pa = warp_append64(keep, &ctl->qa);
-      if (keep) alive2[pa - (long long)base_a] = e;
-      const int mr = __reduce_min_sync(TR_FULL, keep ? r : INT_MAX);
-      if (lane == 0 && mr != INT_MAX) atomicMin(mres, mr);
+      push_items(a, toF, e, wb, F, base_f, s);
+      if (compact) push_alive(a, keep, e, wb, alive2, base_a);
+      wmin = min(wmin, __reduce_min_sync(TR_FULL, keep ? r : INT_MAX));
+      wlive += __popc(__ballot_sync(TR_FULL, keep));
       n_scan += (i < nAlive);
     }
+    flush_items(a, wb, F, base_f);
+    if (compact) flush_alive(a, wb, alive2, base_a);
+    if (lane == 0) {
+      if (wmin != INT_MAX) atomicMin(&s_minres, wmin);
+      if (wlive) atomicAdd(&s_live, wlive);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_minres != INT_MAX) atomicMin(&ctl->minres[slot], s_minres);
+      if (s_live) atomicAdd(&ctl->live[slot], s_live);
+      s_minres = INT_MAX;
+      s_live = 0;
+    }
     if (!grid_barrier(ctl, a.wait_ns, snap)) return;
-    const int minres = __ldcg(mres);
-    const int64_t nF = (int64_t)(snap[0] - base_f), nA = (int64_t)(snap[1] - base_a);
+    const int minres = __ldcg(&ctl->minres[slot]);
+    const int64_t live = __ldcg(&ctl->live[slot]);
+    const int64_t nF = (int64_t)(snap[0] - base_f);
     base_f = snap[0];
-    base_a = snap[1];
+    if (compact) {
+      nAlive = (int64_t)(snap[1] - base_a);
+      base_a = snap[1];
+      int32_t *t = alive;
+      alive = alive2;
+      alive2 = t;
+    }
+    compact = 2 * live <= nAlive;  // rewrite the list when half of it is dead
     sc++;
-    { int32_t *t = alive; alive = alive2; alive2 = t; }
-    nAlive = nA;
     if (nF == 0) {
-      if (nA == 0) break;
+      if (live == 0) break;
       k = minres + 2;  // every alive edge has res >= k-1: skip empty levels
       continue;
     }
@@ -251,34 +383,38 @@ __global__ void __launch_bounds__(kPeelBlock) k_peel(PeelArgs a) {
     for (;;) {
       if (leader && a.trace && ctl->subrounds < a.trace_cap)
         a.trace[ctl->subrounds] = make_int4(k, (int)min(nCur, (int64_t)INT_MAX), 0, 0);
-      const int grp = lane >> 3, j = lane & (kItem - 1);
+      const int grp = lane >> 3, j = lane & 7;
       for (int64_t base = gwarp * 4; base < nCur; base += twarps * 4) {
         const int64_t it = base + grp;
         int e = 0, cnt = 0;
         int64_t lb = 0;
         if (it < nCur) {
-          const int2 item = __ldcg(&F[it]);
+          const int4 item = __ldcg(&F[it]);
           e = item.x;
-          const int start = item.y * kItem;
-          if (item.y == 0 && j == 0) a.truss[e] = k;
-          if (__ldcg(&a.res[e]) > 0) {
-            cnt = min(kItem, __ldg(&a.sup[e]) - start);
-            lb = __ldg(&a.toff[e]) + start;
-          }
+          cnt = item.y & 0xFF;
+          lb = (int64_t)(((uint64_t)(uint32_t)item.w << 32) | (uint32_t)item.z);
+          if ((item.y >> 8) && j == 0) a.truss[e] = k;
         }
-        const bool valid = j < cnt;
-        int2 pr = make_int2(0, 0);
-        if (valid) pr = __ldg(&a.pairs[lb + j]);
-        n_entries += valid ? 1ull : 0ull;
-        charge(a, valid, e, pr, k, s, N, base_f, n_dec);
+        const bool ha = j < cnt, hb = j + 8 < cnt;
+        int2 pa = make_int2(0, 0), pb = make_int2(0, 0);
+        int r = 0;
+        if (ha) {
+          r = __ldcg(&a.res[e]);
+          pa = __ldg(&a.pairs[lb + j]);
+        }
+        if (hb) pb = __ldg(&a.pairs[lb + j + 8]);
+        const bool va = ha && r > 0, vb = hb && r > 0;
+        n_entries += (unsigned long long)(va + vb);
+        charge2(a, e, va, pa, vb, pb, k, s, wb, N, base_f, n_dec);
       }
+      flush_items(a, wb, N, base_f);
       if (!grid_barrier(ctl, a.wait_ns, snap)) return;
       const int64_t nN = (int64_t)(snap[0] - base_f);
       base_f = snap[0];
       s++;
       if (leader) ctl->subrounds++;
       if (nN == 0) break;
-      { int2 *t = F; F = N; N = t; }
+      { int4 *t = F; F = N; N = t; }
       nCur = nN > a.item_cap ? a.item_cap : nN;
       if (nN > a.item_cap && leader) atomicExch(&ctl->err, TRUSS_ECHECK);
     }
@@ -310,9 +446,10 @@ __global__ void k_peel_init(int64_t m, const int32_t *sup, int32_t *res, int32_t
     alive[e] = (int32_t)e;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->minres[0] = INT_MAX;
-    ctl->minres[1] = INT_MAX;
-    ctl->minres[2] = INT_MAX;
+    for (int i = 0; i < 3; i++) {
+      ctl->minres[i] = INT_MAX;
+      ctl->live[i] = 0;
+    }
   }
 }
 
@@ -327,7 +464,7 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
   const int64_t item_cap = m + so.entries / kItem + 64;
   int32_t *res = A.get<int32_t>(m), *stamp = A.get<int32_t>(m);
   int32_t *al0 = A.get<int32_t>(m), *al1 = A.get<int32_t>(m);
-  int2 *Q0 = A.get<int2>(item_cap), *Q1 = A.get<int2>(item_cap);
+  int4 *Q0 = A.get<int4>(item_cap), *Q1 = A.get<int4>(item_cap);
   PeelCtl *ctl = A.get<PeelCtl>(1);
   if (!res || !stamp || !al0 || !al1 || !Q0 || !Q1 || !ctl) return TRUSS_ENOMEM;
   TR_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PeelCtl), s));
@@ -337,8 +474,14 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
   int dev = 0, sms = cfg.sms;
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool one = cfg.blocks_per_sm == 1;
+  const void *kern = one ? (const void *)k_peel<1> : (const void *)k_peel<2>;
   int occ = 0;
-  TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel, kPeelBlock, 0));
+  if (one) {
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<1>, kPeelBlock, 0));
+  } else {
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<2>, kPeelBlock, 0));
+  }
   if (occ < 1) return TRUSS_ECUDA;
   if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < occ) occ = cfg.blocks_per_sm;
   PeelArgs a{};
@@ -363,8 +506,7 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
     a.trace_cap = a.trace ? trace_cap : 0;
   }
   void *args[] = {&a};
-  TR_CUDA(cudaLaunchCooperativeKernel((const void *)k_peel, dim3(sms * occ), dim3(kPeelBlock),
-                                      args, 0, s));
+  TR_CUDA(cudaLaunchCooperativeKernel(kern, dim3(sms * occ), dim3(kPeelBlock), args, 0, s));
   count_launches(1);
   PeelCtl h{};
   TR_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));

@@ -10,11 +10,13 @@
 // oriented edges are cut into ranges of equal total cost (prefix sum plus a
 // binary search per range) and warps take ranges round-robin.  For each
 // vertex u its range touches, the warp stages out(u) in shared memory (if it
-// fits in kWarpCap entries; otherwise it reads it from global memory) and
-// walks the concatenation of the lists out(v), v in its part of out(u), with
-// all 32 lanes busy: a warp prefix sum over the list lengths maps each lane's
-// flat position to (v, position in out(v)).  Membership of w in out(u) is a
-// binary search with a fixed number of steps.
+// fits; otherwise it reads it from global memory).  For each v in its part
+// of out(u) it intersects out(v) with the part of out(u) after v by a warp
+// merge path: out(v) is staged in shared memory in chunks, the window of
+// out(u) is cut to the chunk's value range, and the merged sequence of the
+// two sorted lists is split evenly over the 32 lanes (one binary search per
+// lane on its diagonal, then a branch-free merge), so each list element costs
+// about one step instead of a search.
 //
 // Counts are split by who can see them: supA[e] (e in out(u)) collects the
 // triangles found while u is processed -- in shared memory, then stored once
@@ -28,6 +30,8 @@
 // from the walk of e's tail (shared-memory cursors when one warp walks all of
 // the tail's out-list, else global cursors curA), the rest from global
 // cursors curB.
+#include <climits>
+
 #include "engine.h"
 
 namespace tr {
@@ -42,10 +46,11 @@ template <int MODE>
 struct Cap {
   static constexpr int value = MODE == 0 ? 512 : 256;
 };
+constexpr int kAChunk = 512;  // out(v) entries staged per warp per chunk
 template <int MODE>
 __host__ __device__ constexpr size_t warp_smem() {
-  // L (int32) and counters (int32) or cursors (int64)
-  return (size_t)Cap<MODE>::value * (4 + (MODE == 0 ? 4 : 8));
+  // counters (int32) or cursors (int64), L (int32), out(v) chunk (int32)
+  return (size_t)Cap<MODE>::value * ((MODE == 0 ? 4 : 8) + 4) + (size_t)kAChunk * 4;
 }
 
 struct SupArgs {
@@ -76,72 +81,116 @@ __device__ __forceinline__ int64_t lower_bound64(const int64_t *a, int64_t m, in
 }
 
 // Out-list of u as seen by one warp: staged in shared memory or read from
-// global memory.  Membership is a branch-free lower bound with a fixed number
-// of halving steps (floor(log2 d) + 1), so all lanes of a warp stay in step.
+// global memory.
 struct OutList {
   const int32_t *L;
-  int d, top;  // top = largest power of two <= d
+  int d;
   bool staged;
 
   __device__ __forceinline__ int at(int i) const { return staged ? L[i] : __ldg(&L[i]); }
 
-  // Position of w in out(u), or -1.
-  __device__ __forceinline__ int find(int w) const {
-    int q = 0;  // number of entries < w found so far
-    for (int step = top; step > 0; step >>= 1) {
-      const int nq = q + step;
-      if (nq <= d && at(nq - 1) < w) q = nq;
+  // Lower bound of w in L[lo, d): a branch-free search whose step count
+  // depends only on d - lo, which is the same for every lane of the warp.
+  __device__ __forceinline__ int lower(int lo, int w) const {
+    const int span = d - lo;
+    int q = lo;
+    if (span > 0) {
+      for (int step = 1 << (31 - __clz(span)); step > 0; step >>= 1) {
+        const int nq = q + step;
+        if (nq <= d && at(nq - 1) < w) q = nq;
+      }
     }
-    return (q < d && at(q) == w) ? q : -1;
+    return q;
   }
 };
 
-// Walk edges (u, L[i]) for i in [i0, i1) (i1 <= d-1).  C = owner counters
-// (MODE 0, int32) or owner cursors (MODE 1, int64), bu = offp[u].
+// Record the triangle (u, v, w) found as out(v)[evw - ob] == L[q] while
+// walking edge (u, L[io]).  C = owner counters (MODE 0, int32) or owner
+// cursors (MODE 1, int64).
+template <int MODE>
+__device__ __forceinline__ void found(const SupArgs &a, int64_t bu, void *Cv, int io, int q,
+                                      int64_t evw) {
+  if (MODE == 0) {
+    int32_t *C = (int32_t *)Cv;
+    atomicAdd(&a.supB[evw], 1);
+    atomicAdd(&C[q], 1);
+    atomicAdd(&C[io], 1);
+  } else {
+    unsigned long long *C = (unsigned long long *)Cv;
+    const int64_t euv = bu + io, euw = bu + q;
+    const int64_t x1 = (int64_t)atomicAdd(&C[io], 1ull);
+    const int64_t x2 = (int64_t)atomicAdd(&C[q], 1ull);
+    const int64_t x3 = (int64_t)atomicAdd(&a.curB[evw], 1ull);
+    if (x1 < a.entries && x2 < a.entries && x3 < a.entries) {
+      a.pairs[x1] = make_int2((int)euw, (int)evw);
+      a.pairs[x2] = make_int2((int)euv, (int)evw);
+      a.pairs[x3] = make_int2((int)euv, (int)euw);
+    } else {
+      atomicExch(a.err, TRUSS_ECHECK);
+    }
+  }
+}
+
+// Walk edges (u, L[i]) for i in [i0, i1) (i1 <= d-1); bu = offp[u].
+// For v = L[i], the triangles (u, v, w) are the common entries of out(v) and
+// L[i+1, d).  out(v) is staged chunk by chunk in Abuf; the window of L is cut
+// to [lower(chunk min), lower(chunk max + 1)) and the two sorted runs are
+// intersected by a merge path: lane l takes positions [l*K, (l+1)*K) of the
+// merged order (A first on ties), finds its start by a binary search on its
+// diagonal and then merges K steps; an A entry equal to the current B head
+// is a triangle.
 template <int MODE>
 __device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList &ol, void *Cv,
-                                     int i0, int i1) {
+                                     int i0, int i1, int32_t *Abuf) {
   const int lane = lane_id();
+  const int d = ol.d;
+  const int Lmax = ol.at(d - 1);
   for (int c0 = i0; c0 < i1; c0 += 32) {
     const int i = c0 + lane;
     const bool valid = i < i1;
     const int v = valid ? ol.at(i) : 0;
     const int64_t vb = valid ? __ldg(&a.offp[v]) : 0;
     const int len = valid ? (int)(__ldg(&a.offp[v + 1]) - vb) : 0;
-    const int P = warp_incl_scan(len);
-    const int total = __shfl_sync(TR_FULL, P, 31);
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      const int o = warp_owner(P, t < total ? t : total - 1);
+    const int nv = min(32, i1 - c0);
+    for (int o = 0; o < nv; o++) {
       const int64_t ob = __shfl_sync(TR_FULL, vb, o);
-      const int oP = __shfl_sync(TR_FULL, P, o);
       const int olen = __shfl_sync(TR_FULL, len, o);
-      if (t < total) {
-        const int64_t evw = ob + (t - (oP - olen));
-        const int w = __ldg(&a.adjp[evw]);
-        const int io = c0 + o;
-        const int q = ol.find(w);
-        if (q >= 0) {
-          if (MODE == 0) {
-            int32_t *C = (int32_t *)Cv;
-            atomicAdd(&a.supB[evw], 1);
-            atomicAdd(&C[q], 1);
-            atomicAdd(&C[io], 1);
-          } else {
-            unsigned long long *C = (unsigned long long *)Cv;
-            const int64_t euv = bu + io, euw = bu + q;
-            const int64_t x1 = (int64_t)atomicAdd(&C[io], 1ull);
-            const int64_t x2 = (int64_t)atomicAdd(&C[q], 1ull);
-            const int64_t x3 = (int64_t)atomicAdd(&a.curB[evw], 1ull);
-            if (x1 < a.entries && x2 < a.entries && x3 < a.entries) {
-              a.pairs[x1] = make_int2((int)euw, (int)evw);
-              a.pairs[x2] = make_int2((int)euv, (int)evw);
-              a.pairs[x3] = make_int2((int)euv, (int)euw);
-            } else {
-              atomicExch(a.err, TRUSS_ECHECK);
-            }
+      const int io = c0 + o;
+      int blo = io + 1;
+      for (int cA = 0; cA < olen && blo < d; cA += kAChunk) {
+        const int ac = min(kAChunk, olen - cA);
+        __syncwarp();
+        for (int t = lane; t < ac; t += 32) Abuf[t] = __ldg(&a.adjp[ob + cA + t]);
+        __syncwarp();
+        const int amin = Abuf[0], amax = Abuf[ac - 1];
+        if (amin > Lmax) break;  // nothing later in out(v) can be in out(u)
+        blo = ol.lower(blo, amin);
+        const int bhi = ol.lower(blo, amax + 1);
+        const int bc = bhi - blo;
+        if (bc > 0) {
+          const int total = ac + bc;
+          const int K = (total + 31) >> 5;
+          int p = min(lane * K, total);
+          const int pend = min(p + K, total);
+          // merge-path split of diagonal p: A[0, ia) and B[0, p - ia) come first
+          int lo = max(0, p - bc), hi = min(p, ac);
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (Abuf[mid] <= ol.at(blo + p - 1 - mid)) lo = mid + 1; else hi = mid;
+          }
+          int ia = lo, jb = p - lo;
+          int av = ia < ac ? Abuf[ia] : INT_MAX;
+          int bv = jb < bc ? ol.at(blo + jb) : INT_MAX;
+          for (; p < pend; p++) {
+            const bool takeA = av <= bv;
+            if (takeA && av == bv) found<MODE>(a, bu, Cv, io, blo + jb, ob + cA + ia);
+            ia += takeA;
+            jb += !takeA;
+            av = ia < ac ? Abuf[ia] : INT_MAX;
+            bv = jb < bc ? ol.at(blo + jb) : INT_MAX;
           }
         }
+        blo = bhi;
       }
     }
   }
@@ -149,14 +198,15 @@ __device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList
 
 // Warps take equal-cost ranges of oriented edges round-robin.
 template <int MODE>
-__global__ void __launch_bounds__(kBlock) k_support(SupArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
   constexpr int CAP = Cap<MODE>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
   unsigned char *base = smem_raw + (size_t)warp * warp_smem<MODE>();
-  // layout: counters/cursors (8-byte aligned first), then L
+  // layout: counters/cursors (8-byte aligned first), then L, then the out(v) chunk
   void *Cs = base;
   int32_t *Ls = (int32_t *)(base + (size_t)CAP * (MODE == 0 ? 4 : 8));
+  int32_t *Abuf = Ls + CAP;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = gw; r < a.P; r += nw) {
@@ -175,7 +225,6 @@ __global__ void __launch_bounds__(kBlock) k_support(SupArgs a) {
       const bool whole = i0 == 0 && iend >= d - 1;  // this warp walks all of out(u)
       OutList ol;
       ol.d = d;
-      ol.top = 1 << (31 - __clz(d));
       ol.staged = d <= CAP;
       void *C;
       if (ol.staged) {
@@ -192,7 +241,7 @@ __global__ void __launch_bounds__(kBlock) k_support(SupArgs a) {
         ol.L = a.adjp + bu;
         C = MODE == 0 ? (void *)(a.supA + bu) : (void *)(a.curA + bu);
       }
-      walk<MODE>(a, bu, ol, C, i0, i1);
+      walk<MODE>(a, bu, ol, C, i0, i1, Abuf);
       __syncwarp();
       if (MODE == 0 && ol.staged) {
         const int32_t *Ci = (const int32_t *)Cs;
