@@ -29,6 +29,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gen.c")
 _LIB = os.path.join(_HERE, "libgraphgen.so")
 _lib = None
+_CU_SRC = os.path.join(_HERE, "gen_cuda.cu")
+_CU_LIB = os.path.join(_HERE, "libgraphgen_cuda.so")
+_culib = None
 
 RMAT_ABCD = (Fraction(57, 100), Fraction(19, 100), Fraction(19, 100), Fraction(5, 100))
 TINY_CLIQUES = (8, 12, 16, 20, 24, 32)
@@ -50,6 +53,46 @@ def build(force: bool = False) -> str:
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_cuda(force: bool = False) -> str:
+    """Compile gen_cuda.cu (GPU form of the R-MAT generator) for sm_103a."""
+    if force or not os.path.exists(_CU_LIB) or os.path.getmtime(_CU_LIB) < os.path.getmtime(_CU_SRC):
+        tmp = _CU_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["nvcc", "-O3", "-std=c++17", "-gencode",
+                               "arch=compute_103a,code=sm_103a", "-Xcompiler", "-fPIC", "-shared",
+                               "-o", tmp, _CU_SRC])
+        os.replace(tmp, _CU_LIB)
+    return _CU_LIB
+
+
+def culib():
+    global _culib
+    if _culib is None:
+        build_cuda()
+        L = ctypes.CDLL(_CU_LIB)
+        L.gg_rmat_raw_cuda.restype = ctypes.c_int
+        L.gg_rmat_raw_cuda.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+        _culib = L
+    return _culib
+
+
+def rmat_raw_cuda(scale: int, nsamples: int, seed: int, stream: int = 0, device=None,
+                  cuda_stream=None):
+    """As rmat_raw, generated on the GPU into new torch int32 tensors."""
+    import torch
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    src = torch.empty(nsamples, dtype=torch.int32, device=dev)
+    dst = torch.empty(nsamples, dtype=torch.int32, device=dev)
+    t1, t2, t3 = rmat_thresholds()
+    cs = cuda_stream if cuda_stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    if culib().gg_rmat_raw_cuda(scale, nsamples, t1, t2, t3, seed, stream, src.data_ptr(),
+                                dst.data_ptr(), cs):
+        raise RuntimeError("gg_rmat_raw_cuda failed")
+    return src, dst
 
 
 def lib():
@@ -267,6 +310,14 @@ def serve_schedule(count: int, rate: float = 200.0, mlo: float = 1e3, mhi: float
     m = np.empty(count, np.int64)
     lib().gg_serve_schedule(count, rate, mlo, mhi, seed, _p(t, _f64p), _p(m, _i64p))
     return t, m
+
+
+def serve_scale(m: int) -> int:
+    """R-MAT scale of a served request with target m: ceil(log2(m/8)), >= 4."""
+    scale = 4
+    while (1 << scale) < (m + 7) // 8:
+        scale += 1
+    return scale
 
 
 def serve_request(j: int, m: int, seed: int = 3):

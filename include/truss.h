@@ -142,6 +142,89 @@ typedef struct truss_run_stats {
 /* Statistics of the last successful call on this context. */
 int truss_last_stats(truss_ctx *ctx, truss_run_stats *out);
 
+/* ------------------------------------------------------------- serving --- */
+/* A request loop that decomposes many graphs of mixed sizes concurrently
+ * (each request is the problem of the Section 2 problem definition, solved
+ * as by truss_decompose).  Worker threads, each with its own context and CUDA
+ * stream, take requests in arrival order; waiting requests of at most
+ * `batch_rows` rows are grouped into one batched launch (as
+ * truss_decompose_batch), larger ones run alone, and requests arriving while
+ * others run are admitted as workers and memory free up (continuous
+ * batching).  A request is admitted only while the projected device
+ * footprint of all admitted, unfinished requests stays within
+ * `hbm_budget_bytes` (truss_serve_footprint gives the projection).  Results
+ * are exact and identical to a truss_decompose of the request alone. */
+typedef struct truss_server truss_server;
+
+typedef struct truss_serve_opts {
+  int64_t hbm_budget_bytes; /* 0 = half of the device memory free at start */
+  int32_t max_inflight;     /* admitted, unfinished requests (0 = 256) */
+  int32_t streams;          /* worker threads / streams (0 = 4) */
+  int64_t batch_rows;       /* requests with <= this many rows are batched (0 = 65536) */
+  int32_t max_batch;        /* requests per batched launch (0 = 512) */
+  int32_t max_queue;        /* waiting requests before submit returns TRUSS_EBUSY (0 = 1<<20) */
+  int32_t reserved[6];
+} truss_serve_opts;
+
+typedef struct truss_req_stats {
+  int64_t m;          /* distinct edges */
+  int64_t triangles;  /* triangles */
+  int32_t kmax;       /* max truss number */
+  int32_t batched;    /* requests in the launch that served this one */
+  double queue_ms;    /* submit -> start of its launch */
+  double run_ms;      /* start -> results ready in host memory */
+  double total_ms;    /* submit -> results ready */
+} truss_req_stats;
+
+typedef struct truss_serve_stats {
+  int64_t submitted, admitted, rejected, completed, failed;
+  int64_t edges;            /* distinct edges of completed requests */
+  double p50_ms, p99_ms;    /* submit -> ready latency of completed requests */
+  double mean_ms, max_ms;
+  double wall_s;            /* first submit -> last completion */
+  double edges_per_s;       /* edges / wall_s */
+  int64_t launches;         /* single + batched decompositions run */
+} truss_serve_stats;
+
+/* Projected device footprint (bytes) used for admission of a request of
+ * `rows` rows over `n` vertices: 96 bytes per row for the edge keys, CSR,
+ * supports and peel queues, 16 per vertex, and 8-byte triangle-list entries
+ * for an assumed 3 x 32 triangle incidences per row (the exact figure is
+ * known only after the support pass). */
+int64_t truss_serve_footprint(int64_t n, int64_t rows);
+
+/* Start a server on ctx's device with ctx's options (ctx itself is not used
+ * afterwards and may be destroyed).  opts may be NULL.  Errors: TRUSS_EINVAL,
+ * TRUSS_ECUDA, TRUSS_ENOMEM. */
+int truss_serve_start(truss_ctx *ctx, const truss_serve_opts *opts, truss_server **out);
+
+/* Queue a request.  src/dst (host or device memory, `rows` rows over [0, n))
+ * are read when the request runs, so they must stay valid and unchanged
+ * until the request completes (truss_serve_poll/wait returns TRUSS_OK or an
+ * error for it).  *ticket identifies the request.  Errors: TRUSS_EINVAL (bad
+ * sizes), TRUSS_EBUSY (projected footprint above the whole budget, or queue
+ * full), TRUSS_ESHUTDOWN (server stopping).  Thread-safe. */
+int truss_serve_submit(truss_server *srv, int64_t n, int64_t rows, const int32_t *src,
+                       const int32_t *dst, uint64_t *ticket);
+
+/* If request `ticket` is done, copy its per-row support and truss numbers
+ * into the caller's buffers (host memory, `rows` entries each, either may be
+ * NULL), fill *st (nullable), release the request and return TRUSS_OK (or the
+ * request's own error).  TRUSS_EAGAIN if it is still queued or running;
+ * TRUSS_EINVAL for an unknown ticket.  Thread-safe. */
+int truss_serve_poll(truss_server *srv, uint64_t ticket, int32_t *support_out,
+                     int32_t *truss_out, truss_req_stats *st);
+
+/* As truss_serve_poll, blocking up to timeout_ns (< 0: no limit) for the
+ * request to finish; TRUSS_EAGAIN on timeout.  Thread-safe. */
+int truss_serve_wait(truss_server *srv, uint64_t ticket, int64_t timeout_ns,
+                     int32_t *support_out, int32_t *truss_out, truss_req_stats *st);
+
+/* Stop accepting requests, finish the admitted and queued ones, join the
+ * workers, fill *st (nullable) and free the server (results not yet polled
+ * are discarded).  NULL is accepted. */
+int truss_serve_stop(truss_server *srv, truss_serve_stats *st);
+
 #ifdef __cplusplus
 }
 #endif

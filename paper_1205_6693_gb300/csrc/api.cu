@@ -118,7 +118,33 @@ __global__ void k_batch_kmax(int32_t G, const int64_t *row_off, const int32_t *t
     __syncthreads();
   }
 }
+// Graph of each canonical edge (from its tail's input id) -> per-graph
+// distinct edges and support sums.
+__global__ void k_graph_counts(int64_t m, int32_t G, const int64_t *voff, const int32_t *order,
+                               const int32_t *esrc, const int32_t *sup, unsigned long long *m_g,
+                               unsigned long long *sup_g) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = order[esrc[e]];
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (voff[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    atomicAdd(&m_g[lo], 1ull);
+    atomicAdd(&sup_g[lo], (unsigned long long)sup[e]);
+  }
+}
 }  // namespace
+
+int batch_graph_counts(const Csr &g, int32_t G, const int64_t *voff, const int32_t *sup,
+                       unsigned long long *m_g, unsigned long long *sup_g, cudaStream_t s) {
+  if (g.m == 0 || G <= 0) return TRUSS_OK;
+  k_graph_counts<<<grid_for(g.m, 256, 152 * 16), 256, 0, s>>>(g.m, G, voff, g.order, g.esrc, sup,
+                                                              m_g, sup_g);
+  TR_LAUNCHED();
+  return TRUSS_OK;
+}
 
 int scatter_rows(const Csr &g, const int32_t *sup, const int32_t *truss, int32_t *sup_rows,
                  int32_t *truss_rows, cudaStream_t s) {
@@ -207,7 +233,7 @@ struct Stage {
 int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *src,
                  const int32_t *dst, int32_t G, const int64_t *h_row_off, const int64_t *h_voff,
                  int32_t *support_out, int32_t *truss_out, int32_t *kmax_out, bool want_truss,
-                 cudaStream_t s) {
+                 cudaStream_t s, int64_t *graph_m = nullptr, int64_t *graph_tri = nullptr) {
   TR_CUDA(cudaSetDevice(ctx->device));
   tr::Arena &A = ctx->arena;
   A.reset();
@@ -250,6 +276,20 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   TR_TRY(tr::run_support(A, g, scfg, &so, s));
   sg.mark();  // 2
   st.triangles = so.entries / 3;
+  if (graph_m && h_row_off) {
+    unsigned long long *cnt = A.get<unsigned long long>(2 * (int64_t)G);
+    if (!cnt) return TRUSS_ENOMEM;
+    TR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 2 * G, s));
+    TR_TRY(tr::batch_graph_counts(g, G, d_voff, so.sup, cnt, cnt + G, s));
+    std::vector<unsigned long long> h((size_t)2 * G);
+    TR_CUDA(cudaMemcpyAsync(h.data(), cnt, sizeof(unsigned long long) * 2 * G,
+                            cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaStreamSynchronize(s));
+    for (int32_t i = 0; i < G; i++) {
+      graph_m[i] = (int64_t)h[i];
+      graph_tri[i] = (int64_t)(h[G + i] / 3);
+    }
+  }
 
   int32_t *truss_e = nullptr;
   tr::PeelResult pr;
@@ -333,6 +373,37 @@ int check_common(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, co
 }
 
 }  // namespace
+
+namespace tr {
+// Batched decomposition with per-graph distinct-edge and triangle counts
+// (host arrays of G entries); used by the request server.
+int decompose_batch_counts(truss_ctx *ctx, int32_t G, const int64_t *n, const int64_t *row_off,
+                           const int32_t *src, const int32_t *dst, int32_t *support_out,
+                           int32_t *truss_out, int32_t *kmax_out, cudaStream_t s,
+                           int64_t *graph_m, int64_t *graph_tri) {
+  std::vector<int64_t> voff((size_t)G + 1, 0);
+  for (int32_t g = 0; g < G; g++) voff[g + 1] = voff[g] + n[g];
+  const int64_t rows = row_off[G];
+  if (rows == 0) {
+    for (int32_t g = 0; g < G; g++) {
+      if (kmax_out) kmax_out[g] = 0;
+      graph_m[g] = graph_tri[g] = 0;
+    }
+    return TRUSS_OK;
+  }
+  return run_pipeline(ctx, voff[G], rows, src, dst, G, row_off, voff.data(), support_out,
+                      truss_out, kmax_out, true, s, graph_m, graph_tri);
+}
+int ctx_device(truss_ctx *ctx) { return ctx->device; }
+// Release the context's workspace if it holds more than max_bytes.
+void ctx_trim(truss_ctx *ctx, size_t max_bytes) {
+  if (ctx->arena.reserved() > max_bytes) {
+    cudaSetDevice(ctx->device);
+    ctx->arena.release_all();
+  }
+}
+const truss_opts *ctx_opts(truss_ctx *ctx) { return &ctx->opts; }
+}  // namespace tr
 
 extern "C" {
 

@@ -213,6 +213,7 @@ int build_csr(Arena &A, const RowsIn &in, Csr *out, int32_t *d_err, cudaStream_t
   if (!tmp) return TRUSS_ENOMEM;
   TR_TRY(sort_pairs_u32(tmp, &tb, (const uint32_t *)deg, (uint32_t *)sdeg, ids, order, n, 0, db,
                         s));
+  out->order = order;
   k_newid<<<grid_for(n, kBlock, maxg), kBlock, 0, s>>>(n, order, newid);
   TR_LAUNCHED();
 

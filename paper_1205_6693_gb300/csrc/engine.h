@@ -75,6 +75,7 @@ struct Csr {
   int32_t *adjp = nullptr;   // [m]   head (higher-ranked endpoint) of edge e
   int32_t *esrc = nullptr;   // [m]   tail (lower-ranked endpoint) of edge e
   int32_t *row2e = nullptr;  // [rows] row -> e, -1 for self-loop rows
+  int32_t *order = nullptr;  // [n]   rank -> input vertex id
 };
 
 struct DevCounters;  // device scratch for small counters (api.cu)
@@ -125,6 +126,10 @@ int scatter_rows(const Csr &g, const int32_t *sup, const int32_t *truss, int32_t
                  int32_t *truss_rows, cudaStream_t s);
 int batch_kmax(int32_t G, const int64_t *row_off, const int32_t *truss_rows, int32_t *kmax,
                cudaStream_t s);
+// Per-graph distinct edges and support sums of a batch (voff: device vertex
+// offsets, G+1 entries); results are added into m_g and sup_g (device, G).
+int batch_graph_counts(const Csr &g, int32_t G, const int64_t *voff, const int32_t *sup,
+                       unsigned long long *m_g, unsigned long long *sup_g, cudaStream_t s);
 
 // Algorithmic byte counts (see the comments in support.cu / peel.cu).
 int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, double *b_sup,

@@ -59,6 +59,35 @@ class truss_run_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class truss_serve_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("batch_rows", ctypes.c_int64),
+                ("max_batch", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class truss_req_stats(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("triangles", ctypes.c_int64), ("kmax", ctypes.c_int32),
+                ("batched", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class truss_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("edges", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("wall_s", ctypes.c_double), ("edges_per_s", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _LIB = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -66,7 +95,9 @@ _i32 = ctypes.c_int32
 
 # Symbols declared in include/truss.h (checked by the CPU test suite).
 EXPORTS = ("truss_strerror", "truss_ctx_create", "truss_ctx_destroy", "truss_support",
-           "truss_decompose", "truss_decompose_batch", "truss_last_stats")
+           "truss_decompose", "truss_decompose_batch", "truss_last_stats",
+           "truss_serve_footprint", "truss_serve_start", "truss_serve_submit", "truss_serve_poll",
+           "truss_serve_wait", "truss_serve_stop")
 
 
 def library_path() -> str:
@@ -97,6 +128,20 @@ def _lib():
         L.truss_decompose_batch.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.truss_last_stats.restype = ctypes.c_int
         L.truss_last_stats.argtypes = [_vp, ctypes.POINTER(truss_run_stats)]
+        L.truss_serve_footprint.restype = ctypes.c_int64
+        L.truss_serve_footprint.argtypes = [_i64, _i64]
+        L.truss_serve_start.restype = ctypes.c_int
+        L.truss_serve_start.argtypes = [_vp, ctypes.POINTER(truss_serve_opts), ctypes.POINTER(_vp)]
+        L.truss_serve_submit.restype = ctypes.c_int
+        L.truss_serve_submit.argtypes = [_vp, _i64, _i64, _vp, _vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.truss_serve_poll.restype = ctypes.c_int
+        L.truss_serve_poll.argtypes = [_vp, ctypes.c_uint64, _vp, _vp,
+                                       ctypes.POINTER(truss_req_stats)]
+        L.truss_serve_wait.restype = ctypes.c_int
+        L.truss_serve_wait.argtypes = [_vp, ctypes.c_uint64, _i64, _vp, _vp,
+                                       ctypes.POINTER(truss_req_stats)]
+        L.truss_serve_stop.restype = ctypes.c_int
+        L.truss_serve_stop.argtypes = [_vp, ctypes.POINTER(truss_serve_stats)]
         _LIB = L
     return _LIB
 
@@ -192,6 +237,54 @@ def truss_decompose_batch(ctx, n, row_off, src, dst, support_out, truss_out, kma
 def truss_last_stats(ctx) -> dict:
     st = truss_run_stats()
     _check(_lib().truss_last_stats(ctx, ctypes.byref(st)), "truss_last_stats")
+    return st.as_dict()
+
+
+# ---------------------------------------------------------------- serving ---
+def truss_serve_footprint(n: int, rows: int) -> int:
+    return int(_lib().truss_serve_footprint(n, rows))
+
+
+def truss_serve_start(ctx, opts: truss_serve_opts | None = None):
+    srv = _vp()
+    _check(_lib().truss_serve_start(ctx, ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(srv)), "truss_serve_start")
+    return srv
+
+
+def truss_serve_submit(srv, n: int, src, dst) -> int:
+    """Queue a request; src/dst must stay alive until it completes."""
+    t = ctypes.c_uint64(0)
+    _check(_lib().truss_serve_submit(srv, n, _len(src), _ptr(src), _ptr(dst), ctypes.byref(t)),
+           "truss_serve_submit")
+    return int(t.value)
+
+
+def truss_serve_poll(srv, ticket: int, support_out=None, truss_out=None):
+    """Returns the request's stats dict if done, None if still running."""
+    st = truss_req_stats()
+    rc = _lib().truss_serve_poll(srv, ticket, _ptr(support_out), _ptr(truss_out),
+                                 ctypes.byref(st))
+    if rc == TRUSS_EAGAIN:
+        return None
+    _check(rc, "truss_serve_poll")
+    return st.as_dict()
+
+
+def truss_serve_wait(srv, ticket: int, timeout_ns: int = -1, support_out=None, truss_out=None):
+    """Blocks until done (or timeout: returns None)."""
+    st = truss_req_stats()
+    rc = _lib().truss_serve_wait(srv, ticket, timeout_ns, _ptr(support_out), _ptr(truss_out),
+                                 ctypes.byref(st))
+    if rc == TRUSS_EAGAIN:
+        return None
+    _check(rc, "truss_serve_wait")
+    return st.as_dict()
+
+
+def truss_serve_stop(srv) -> dict:
+    st = truss_serve_stats()
+    _check(_lib().truss_serve_stop(srv, ctypes.byref(st)), "truss_serve_stop")
     return st.as_dict()
 
 

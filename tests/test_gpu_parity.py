@@ -223,3 +223,11 @@ def test_large_full_size(ctx):
     if "large" not in json.load(open(os.path.join(GOLDEN, "digests.json"))):
         pytest.skip("no stored oracle digest for the large workload")
     _check_full(ctx, "large", graphgen.large)
+
+
+def test_gpu_generator_matches_cpu_generator():
+    s_cpu, d_cpu = graphgen.rmat_raw(16, 1 << 20, seed=11, stream=2)
+    s_gpu, d_gpu = graphgen.rmat_raw_cuda(16, 1 << 20, seed=11, stream=2)
+    torch.cuda.synchronize()
+    assert np.array_equal(s_gpu.cpu().numpy(), s_cpu)
+    assert np.array_equal(d_gpu.cpu().numpy(), d_cpu)
