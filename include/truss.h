@@ -142,6 +142,37 @@ typedef struct truss_run_stats {
 /* Statistics of the last successful call on this context. */
 int truss_last_stats(truss_ctx *ctx, truss_run_stats *out);
 
+/* ------------------------------------------------ allocation-free support --- */
+/* Largest graph truss_support_noalloc accepts. */
+#define TRUSS_NOALLOC_MAX_ROWS 65536
+#define TRUSS_NOALLOC_MAX_N 65536
+
+/* Per-row edge support, as truss_support, for a small graph and without
+ * allocating any memory.  The paper has no counterpart to this entry point.
+ * It is for callers that cannot allocate at the moment they need the result
+ * and so cannot use a truss_ctx, whose workspace is allocated on demand: code
+ * running inside an allocator or memory-pool callback, or a process whose
+ * device memory is entirely handed out by another allocator.
+ *
+ * All working memory is one fixed array of about 5 MB in the library's device
+ * image: every GPU that loads the library holds it until the process exits.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * on a device uses the same array and clears what it reads, so calls whose
+ * work can overlap on the GPU (other streams, other host threads) race on it
+ * and must be serialised by the caller.
+ *
+ * n must be <= TRUSS_NOALLOC_MAX_N and rows <= TRUSS_NOALLOC_MAX_ROWS;
+ * anything larger is rejected with TRUSS_EINVAL before any device work.
+ * src, dst and support_out must be device-accessible (device, managed or
+ * mapped pinned memory); support_out[r] is the support of row r's edge, -1 for
+ * a self-loop row.  The work runs on the current device on cuda_stream and the
+ * call waits for it (it reads back one status word).  Errors: TRUSS_EINVAL
+ * (sizes, null or host-only pointers, a vertex id outside [0, n)),
+ * TRUSS_ECUDA. */
+int truss_support_noalloc(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+                          int32_t *support_out, void *cuda_stream);
+
 /* ------------------------------------------------------------- serving --- */
 /* A request loop that decomposes many graphs of mixed sizes concurrently
  * (each request is the problem of the Section 2 problem definition, solved

@@ -97,7 +97,7 @@ _i32 = ctypes.c_int32
 EXPORTS = ("truss_strerror", "truss_ctx_create", "truss_ctx_destroy", "truss_support",
            "truss_decompose", "truss_decompose_batch", "truss_last_stats",
            "truss_serve_footprint", "truss_serve_start", "truss_serve_submit", "truss_serve_poll",
-           "truss_serve_wait", "truss_serve_stop")
+           "truss_serve_wait", "truss_serve_stop", "truss_support_noalloc")
 
 
 def library_path() -> str:
@@ -140,6 +140,8 @@ def _lib():
         L.truss_serve_wait.restype = ctypes.c_int
         L.truss_serve_wait.argtypes = [_vp, ctypes.c_uint64, _i64, _vp, _vp,
                                        ctypes.POINTER(truss_req_stats)]
+        L.truss_support_noalloc.restype = ctypes.c_int
+        L.truss_support_noalloc.argtypes = [_i64, _i64, _vp, _vp, _vp, _vp]
         L.truss_serve_stop.restype = ctypes.c_int
         L.truss_serve_stop.argtypes = [_vp, ctypes.POINTER(truss_serve_stats)]
         _LIB = L
@@ -238,6 +240,14 @@ def truss_last_stats(ctx) -> dict:
     st = truss_run_stats()
     _check(_lib().truss_last_stats(ctx, ctypes.byref(st)), "truss_last_stats")
     return st.as_dict()
+
+
+def truss_support_noalloc(n: int, src, dst, support_out, stream=None) -> None:
+    """Allocation-free support for small graphs (device-accessible buffers;
+    see include/truss.h for the size limits and the shared-scratch rules)."""
+    _check(_lib().truss_support_noalloc(n, _len(src), _ptr(src), _ptr(dst), _ptr(support_out),
+                                        _stream(stream, src, support_out)),
+           "truss_support_noalloc")
 
 
 # ---------------------------------------------------------------- serving ---
