@@ -6,6 +6,7 @@ edge-factor-16 graph ((a,b,c,d) = (.57,.19,.19,.05), seed 1; 16,777,216 raw
 rows, 15,702,720 distinct undirected edges), inputs resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--mode single|batch|serve]
 
 Prints ONE JSON line (rank 0).  `value` is distinct edges decomposed per second
 summed over ranks (each rank decomposes its own replica: one graph does not
@@ -15,6 +16,14 @@ dominant kernel's algorithmic bytes over its CUDA-event duration against the
 measured HBM copy bandwidth.  `cpu_baseline` is the CPU oracle (single
 thread) on a bounded prefix of the same rows.  `--impl reference` times that
 oracle as the reference arm.
+
+`--mode batch` times truss_decompose_batch on the 4,096-graph mixed batch
+(graphs/s) against a loop of per-graph truss_decompose calls; `--mode serve`
+replays a Poisson request stream (200 req/s, R-MAT requests generated on the
+GPU) through the truss_serve_* server and reports p50/p99 latency and
+achieved vs offered edges/s.  Under torchrun each rank takes its own share of
+the graphs (batch) or runs its own server on its own stream (serve); no
+collective touches the data path.
 """
 from __future__ import annotations
 
@@ -39,7 +48,7 @@ UNIT = "edges/s"
 WORKLOAD = ("mid: R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 1; "
             "16,777,216 raw rows -> 15,702,720 distinct undirected edges; int32 ids, "
             "int64 CSR offsets")
-CPU_SAMPLE_ROWS = 3_000_000     # cpu_baseline: oracle on this prefix of the rows
+CPU_SAMPLE_ROWS = 8_000_000     # cpu_baseline: oracle on this prefix of the rows
 REF_SAMPLE_ROWS = 1_000_000     # --impl reference: oracle per step on this prefix
 L2_FLUSH_BYTES = 512 << 20
 
@@ -156,6 +165,170 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def _dist_init(ws, local):
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    return dev, dist
+
+
+def _max_over_ranks(dist, dev, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_batch(args, ws, rank, local):
+    """Batched form: the mixed 4,096-graph batch in one truss_decompose_batch
+    call, against per-graph truss_decompose calls on the same stream."""
+    import torch
+    from paper_1205_6693_gb300 import truss as T
+    from paper_1205_6693_gb300.shard import shard_range
+    dev, dist = _dist_init(ws, local)
+    g0, g1 = shard_range(args.graphs, rank, ws)
+    ns, off, src_np, dst_np = graphgen.batch(g1 - g0, first=g0)
+    G = len(ns)
+    src = torch.from_numpy(src_np).to(dev)
+    dst = torch.from_numpy(dst_np).to(dev)
+    sup = torch.empty_like(src)
+    tr = torch.empty_like(src)
+    kmax = torch.empty(G, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx = T.Context(local, profile=True)
+    for _ in range(args.warmup):
+        ctx.decompose_batch(ns, off, src, dst, sup, tr, kmax, stream=stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = 0.0
+    launches = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.decompose_batch(ns, off, src, dst, sup, tr, kmax, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += e0.elapsed_time(e1)
+        launches += ctx.stats()["launches"]
+    st = ctx.stats()
+    ms = _max_over_ranks(dist, dev, ms)
+    # per-graph plain launches (one pass; same stream, same device buffers)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for g in range(G):
+        a, b = int(off[g]), int(off[g + 1])
+        ctx.decompose(int(ns[g]), src[a:b], dst[a:b], sup[a:b], tr[a:b], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    loop_ms = _max_over_ranks(dist, dev, e0.elapsed_time(e1))
+    ctx.close()
+    if rank == 0:
+        value = args.graphs * args.steps / (ms / 1e3)
+        line = {"metric": "batched graphs/s (bit-exact truss decomposition)", "value": value,
+                "unit": "graphs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": (f"{args.graphs} graphs: ER / R-MAT / ER+clique, edges "
+                                        "log-uniform in [64, 65536], seed SplitMix64(0xB47C^g)"),
+                           "rows": int(off[-1]) * ws, "edges_rank0": st["m"],
+                           "triangles_rank0": st["triangles"],
+                           "parallelism": f"graphs sharded over {ws} rank(s)",
+                           "l2_flush": True},
+                "per_graph_loop": {"value": args.graphs / (loop_ms / 1e3), "unit": "graphs/s",
+                                   "ms": loop_ms},
+                "speedup_vs_loop": (args.graphs * args.steps / (ms / 1e3))
+                / (args.graphs / (loop_ms / 1e3)),
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_serve(args, ws, rank, local):
+    """Served form: Poisson arrivals replayed in real time through the server."""
+    import threading
+    import torch
+    from paper_1205_6693_gb300 import truss as T
+    dev, dist = _dist_init(ws, local)
+    count = max(1, int(args.rate * args.window))
+    t_arr, m_req = graphgen.serve_schedule(count * ws, rate=args.rate * ws)
+    mine = list(range(rank, count * ws, ws))
+    reqs = []
+    for j in mine:
+        m = int(m_req[j])
+        scale = graphgen.serve_scale(m)
+        s, d = graphgen.rmat_raw_cuda(scale, m, seed=graphgen.gg_seed(3, j), device=dev)
+        reqs.append((j, 1 << scale, s, d))
+    torch.cuda.synchronize(dev)
+    ctx = T.truss_ctx_create(local)
+    opts = T.truss_serve_opts()
+    opts.streams = 4
+    srv = T.truss_serve_start(ctx, opts)
+    T.truss_ctx_destroy(ctx)
+    # warm-up: a few requests outside the timed stream
+    for j, n, s, d in reqs[: min(4, len(reqs))]:
+        T.truss_serve_wait(srv, T.truss_serve_submit(srv, n, s, d))
+    T.truss_serve_stop(srv)
+    ctx = T.truss_ctx_create(local)
+    srv = T.truss_serve_start(ctx, opts)
+    T.truss_ctx_destroy(ctx)
+    if dist:
+        dist.barrier()
+    tickets = [None] * len(reqs)
+    delay = [0.0] * len(reqs)
+    t0 = time.perf_counter()
+
+    def client():
+        for i, (j, n, s, d) in enumerate(reqs):
+            wait = t_arr[j] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            delay[i] = (time.perf_counter() - t0) - t_arr[j]
+            tickets[i] = T.truss_serve_submit(srv, n, s, d)
+
+    th = threading.Thread(target=client)
+    th.start()
+    lat, m_done = [], 0
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        st = T.truss_serve_wait(srv, tickets[i])
+        lat.append(st["total_ms"] + 1e3 * delay[i])  # from the scheduled arrival
+        m_done += st["m"]
+    th.join()
+    wall = time.perf_counter() - t0
+    stats = T.truss_serve_stop(srv)
+    offered = float(sum(int(m_req[j]) for j in mine)) / args.window
+    lat.sort()
+    p = lambda q: lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))]
+    if rank == 0:
+        line = {"metric": "served p99 latency (bit-exact truss decomposition)",
+                "value": p(0.99), "unit": "ms", "n_gpus": ws, "steps": len(reqs),
+                "warmup": min(4, len(reqs)), "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": (f"Poisson {args.rate:g} req/s for {args.window:g} s, "
+                                        "R-MAT requests, raw samples log-uniform in [1e3, 5e7]"),
+                           "requests": len(reqs), "streams": opts.streams},
+                "p50_ms": p(0.50), "p99_ms": p(0.99), "mean_ms": sum(lat) / len(lat),
+                "achieved_edges_per_s": m_done / wall, "offered_samples_per_s": offered,
+                "server": stats}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,10 +336,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--graphs", type=int, default=4096, help="batch mode: graphs")
+    ap.add_argument("--window", type=float, default=1.0, help="serve mode: arrival window (s)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve mode: requests per second")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.mode == "batch":
+        return run_batch(args, ws, rank, local)
+    if args.mode == "serve":
+        return run_serve(args, ws, rank, local)
 
     import torch
     from paper_1205_6693_gb300 import truss as T
@@ -263,8 +444,8 @@ def main():
     dom = max(cand, key=lambda k: cand[k][0])
     dms, dbytes = cand[dom]
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
-    kernel_name = {"support": "k_support_warp<0> (+ k_support_block<0>)",
-                   "lists": "k_support_warp<1> (+ k_support_block<1>)",
+    kernel_name = {"support": "k_support<0>",
+                   "lists": "k_support<1>",
                    "peel": "k_peel (persistent, cooperative)"}[dom]
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")

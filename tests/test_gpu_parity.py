@@ -231,3 +231,27 @@ def test_gpu_generator_matches_cpu_generator():
     torch.cuda.synchronize()
     assert np.array_equal(s_gpu.cpu().numpy(), s_cpu)
     assert np.array_equal(d_gpu.cpu().numpy(), d_cpu)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    # A 1 ns limit on the peel kernel's grid barrier makes waiting blocks give
+    # up at once: the kernel must return TRUSS_ETIMEOUT, not hang, and both
+    # this context and a fresh one must still work afterwards.
+    from paper_1205_6693_gb300 import truss as T
+    n, (src, dst) = 2 ** 12, graphgen.rmat_raw(12, 16 * 2 ** 12, seed=9)
+    c = T.Context(0, wait_limit_ns=1)
+    try:
+        with pytest.raises(T.TrussError) as ei:
+            gpu_run(c, n, src, dst)
+        assert ei.value.code == T.TRUSS_ETIMEOUT
+        # support does not use the grid barrier and still works on this context
+        ref = oracle.truss(n, src, dst)
+        sup, _, _ = gpu_run(c, n, src, dst, support_only=True)
+        assert np.array_equal(sup, ref.support)
+    finally:
+        c.close()
+    c2 = T.Context(0)
+    try:
+        assert_same(c2, n, src, dst)
+    finally:
+        c2.close()
