@@ -61,6 +61,12 @@ void Arena::reset() {
   for (auto &c : chunks_) c.used = 0;
 }
 
+size_t Arena::unused() const {
+  size_t s = 0;
+  for (auto &c : chunks_) s += c.cap - c.used;
+  return s;
+}
+
 size_t Arena::reserved() const {
   size_t s = 0;
   for (auto &c : chunks_) s += c.cap;
@@ -272,6 +278,7 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
 
   tr::SupportCfg scfg;
   scfg.sms = ctx->sms;
+  scfg.records = want_truss;
   tr::SupportOut so;
   TR_TRY(tr::run_support(A, g, scfg, &so, s));
   sg.mark();  // 2

@@ -29,6 +29,7 @@ class Arena {
     return static_cast<T *>(alloc(sizeof(T) * (size_t)(count > 0 ? count : 1)));
   }
   size_t reserved() const;
+  size_t unused() const;  // bytes of reserved chunks not handed out since reset()
   void release_all();
 
  private:
@@ -90,11 +91,16 @@ struct SupportOut {
   int64_t *wpre = nullptr;   // [m+1] exclusive prefix of the per-edge walk cost
   int64_t walk = 0;          // total walk cost (entries of out-lists scanned)
   int64_t entries = 0;       // sum sup = 3 * triangles
+  // optional triangle records of the support walk (see support.cu)
+  int64_t *tbpre = nullptr;  // [m+1] record-region offsets
+  int2 *tb = nullptr;        // (e_uw, e_vw) records per walked edge e_uv
+  int32_t *cuv = nullptr;    // [m] records per edge
 };
 
 struct SupportCfg {
   int block = 256;
   int sms = 0;
+  bool records = false;  // also record triangles for the list pass (if memory allows)
 };
 
 // Support of every edge: sup = supA + supB (support.cu).

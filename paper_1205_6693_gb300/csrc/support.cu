@@ -68,6 +68,11 @@ struct SupArgs {
   int2 *pairs;          // MODE 1
   int64_t entries;      // MODE 1: size of pairs (writes beyond it are dropped)
   int *err;             // MODE 1: set to TRUSS_ECHECK if a list would overflow
+  // MODE 0, optional: per walked edge e = (u, v), the triangles (u, v, w) it
+  // closes, as (e_uw, e_vw) records in tb[tbpre[e] .. tbpre[e] + cuv[e]).
+  const int64_t *tbpre;  // [m+1] exclusive prefix of min(|out(v)|, |out(u) after v|)
+  int2 *tb;
+  int32_t *cuv;
 };
 
 // First e in [0, m] with wpre[e] >= x.
@@ -109,12 +114,19 @@ struct OutList {
 // cursors (MODE 1, int64).
 template <int MODE>
 __device__ __forceinline__ void found(const SupArgs &a, int64_t bu, void *Cv, int io, int q,
-                                      int64_t evw) {
+                                      int64_t evw, int *uvc) {
   if (MODE == 0) {
     int32_t *C = (int32_t *)Cv;
     atomicAdd(&a.supB[evw], 1);
     atomicAdd(&C[q], 1);
-    atomicAdd(&C[io], 1);
+    if (a.tb) {
+      // record the triangle under e_uv; C[io] gets the pair's total later
+      const int64_t euv = bu + io;
+      const int r = atomicAdd(uvc, 1);
+      a.tb[__ldg(&a.tbpre[euv]) + r] = make_int2((int)(bu + q), (int)evw);
+    } else {
+      atomicAdd(&C[io], 1);
+    }
   } else {
     unsigned long long *C = (unsigned long long *)Cv;
     const int64_t euv = bu + io, euw = bu + q;
@@ -141,7 +153,7 @@ __device__ __forceinline__ void found(const SupArgs &a, int64_t bu, void *Cv, in
 // is a triangle.
 template <int MODE>
 __device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList &ol, void *Cv,
-                                     int i0, int i1, int32_t *Abuf) {
+                                     int i0, int i1, int32_t *Abuf, int *uvc) {
   const int lane = lane_id();
   const int d = ol.d;
   const int Lmax = ol.at(d - 1);
@@ -183,7 +195,7 @@ __device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList
           int bv = jb < bc ? ol.at(blo + jb) : INT_MAX;
           for (; p < pend; p++) {
             const bool takeA = av <= bv;
-            if (takeA && av == bv) found<MODE>(a, bu, Cv, io, blo + jb, ob + cA + ia);
+            if (takeA && av == bv) found<MODE>(a, bu, Cv, io, blo + jb, ob + cA + ia, uvc);
             ia += takeA;
             jb += !takeA;
             av = ia < ac ? Abuf[ia] : INT_MAX;
@@ -191,6 +203,17 @@ __device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList
           }
         }
         blo = bhi;
+      }
+      if (MODE == 0 && a.tb) {
+        // close the pair (u, v): its record count, and its owner count C[io]
+        __syncwarp();
+        if (lane == 0) {
+          const int tot = *uvc;
+          a.cuv[bu + io] = tot;
+          if (tot) atomicAdd(&((int32_t *)Cv)[io], tot);
+          *uvc = 0;
+        }
+        __syncwarp();
       }
     }
   }
@@ -207,6 +230,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
   void *Cs = base;
   int32_t *Ls = (int32_t *)(base + (size_t)CAP * (MODE == 0 ? 4 : 8));
   int32_t *Abuf = Ls + CAP;
+  __shared__ int s_uvc[kBlock / 32];
+  int *uvc = &s_uvc[warp];
+  if (lane == 0) *uvc = 0;
+  __syncwarp();
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = gw; r < a.P; r += nw) {
@@ -241,7 +268,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
         ol.L = a.adjp + bu;
         C = MODE == 0 ? (void *)(a.supA + bu) : (void *)(a.curA + bu);
       }
-      walk<MODE>(a, bu, ol, C, i0, i1, Abuf);
+      walk<MODE>(a, bu, ol, C, i0, i1, Abuf, uvc);
       __syncwarp();
       if (MODE == 0 && ol.staged) {
         const int32_t *Ci = (const int32_t *)Cs;
@@ -256,21 +283,73 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
 }
 
 // Walk cost of each oriented edge: |out(v)| for (u, v) unless v is the last
-// entry of out(u).
+// entry of out(u); and the most triangles (u, v, w) it can close,
+// min(|out(v)|, entries of out(u) after v).
 __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
-                            const int32_t *esrc, int64_t *cost) {
+                            const int32_t *esrc, int64_t *cost, int64_t *bound) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t c = 0;
+    int64_t c = 0, b = 0;
     if (e < m) {
       const int u = esrc[e];
-      if (e != offp[u + 1] - 1) {
+      const int64_t end = offp[u + 1];
+      if (e != end - 1) {
         const int v = adjp[e];
         c = offp[v + 1] - offp[v];
+        b = min(c, end - 1 - e);
       }
     }
     cost[e] = c;
+    bound[e] = b;
   }
+}
+
+// Dense triangle lists from the per-edge records: e's own records go first
+// (list slots known), the two partners take a slot from their cursors
+// (starting after their own records).
+__global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2 *tb,
+                                     const int32_t *cuv, const int64_t *toff,
+                                     unsigned long long *cur, int2 *pairs, int64_t entries,
+                                     int *err) {
+  const int lane = lane_id();
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gw * 32; base < m; base += nw * 32) {
+    const int64_t e = base + lane;
+    const int c = e < m ? cuv[e] : 0;
+    const int64_t r0 = e < m ? tbpre[e] : 0, l0 = e < m ? toff[e] : 0;
+    const int P = warp_incl_scan(c);
+    const int total = __shfl_sync(TR_FULL, P, 31);
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      const int o = warp_owner(P, t < total ? t : total - 1);
+      const int64_t orr = __shfl_sync(TR_FULL, r0, o), ol = __shfl_sync(TR_FULL, l0, o);
+      const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
+      if (t < total) {
+        const int j = t - (oP - oc);
+        const int eo = (int)(base + o);
+        const int2 rec = __ldg(&tb[orr + j]);  // (e_uw, e_vw) of triangle on e_uv = eo
+        const int64_t x1 = ol + j;
+        const int64_t x2 = (int64_t)atomicAdd(&cur[rec.x], 1ull);
+        const int64_t x3 = (int64_t)atomicAdd(&cur[rec.y], 1ull);
+        if (x1 < entries && x2 < entries && x3 < entries) {
+          pairs[x1] = rec;
+          pairs[x2] = make_int2(eo, rec.y);
+          pairs[x3] = make_int2(eo, rec.x);
+        } else {
+          atomicExch(err, TRUSS_ECHECK);
+        }
+      }
+    }
+  }
+}
+
+// Cursors for k_lists_from_records: after each edge's own records.
+__global__ void k_cursors_rec(int64_t m, const int64_t *toff, const int32_t *cuv,
+                              unsigned long long *cur) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    cur[e] = (unsigned long long)(toff[e] + cuv[e]);
 }
 
 __global__ void k_sum(int64_t m, const int32_t *supA, const int32_t *supB, int32_t *sup,
@@ -303,6 +382,12 @@ int launch_walk(int mode, SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const size_t smem = (size_t)(kBlock / 32) * (mode == 0 ? warp_smem<0>() : warp_smem<1>());
+  // the per-warp buffers (dynamic) plus small static counters exceed the
+  // default 48 KB window: opt in to the larger per-block limit
+  TR_CUDA(cudaFuncSetAttribute(k_support<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kBlock / 32 * warp_smem<0>())));
+  TR_CUDA(cudaFuncSetAttribute(k_support<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kBlock / 32 * warp_smem<1>())));
   int occ = 0;
   if (mode == 0) {
     TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_support<0>, kBlock, smem));
@@ -329,20 +414,49 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
   int32_t *supA = A.get<int32_t>(m), *supB = A.get<int32_t>(m), *sup = A.get<int32_t>(m);
   int64_t *sup64 = A.get<int64_t>(m + 1), *toff = A.get<int64_t>(m + 1);
   int64_t *wcost = A.get<int64_t>(m + 1), *wpre = A.get<int64_t>(m + 1);
-  if (!supA || !supB || !sup || !sup64 || !toff || !wcost || !wpre) return TRUSS_ENOMEM;
+  int64_t *wbound = A.get<int64_t>(m + 1), *tbpre = A.get<int64_t>(m + 1);
+  if (!supA || !supB || !sup || !sup64 || !toff || !wcost || !wpre || !wbound || !tbpre)
+    return TRUSS_ENOMEM;
   TR_CUDA(cudaMemsetAsync(supA, 0, sizeof(int32_t) * m, s));
   TR_CUDA(cudaMemsetAsync(supB, 0, sizeof(int32_t) * m, s));
-  int64_t W = 0;
+  int64_t W = 0, R = 0;
   if (m > 0) {
-    k_walk_cost<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, g.offp, g.adjp, g.esrc, wcost);
+    k_walk_cost<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, g.offp, g.adjp, g.esrc, wcost,
+                                                                wbound);
     TR_LAUNCHED();
     size_t tb = 0;
     TR_TRY(exclusive_sum_i64(nullptr, &tb, wcost, wpre, m + 1, s));
     void *tmp = A.alloc(tb);
     if (!tmp) return TRUSS_ENOMEM;
     TR_TRY(exclusive_sum_i64(tmp, &tb, wcost, wpre, m + 1, s));
+    if (cfg.records) TR_TRY(exclusive_sum_i64(tmp, &tb, wbound, tbpre, m + 1, s));
     TR_CUDA(cudaMemcpyAsync(&W, wpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (cfg.records)
+      TR_CUDA(cudaMemcpyAsync(&R, tbpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TR_CUDA(cudaStreamSynchronize(s));
+  }
+  // Records need 8 R bytes now and the lists later at most 24 R more; use
+  // them only when that fits in free device memory (else the list pass walks
+  // the graph a second time).
+  int2 *recs = nullptr;
+  int32_t *cuv = nullptr;
+  if (cfg.records && R > 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = 0;
+    }
+    const double need = 32.0 * (double)R + 4.0 * (double)m;
+    if (need * 1.05 < (double)fr + (double)A.unused()) {
+      recs = A.get<int2>(R);
+      cuv = A.get<int32_t>(m);
+      if (!recs || !cuv) {
+        recs = nullptr;
+        cuv = nullptr;
+      } else {
+        TR_CUDA(cudaMemsetAsync(cuv, 0, sizeof(int32_t) * m, s));
+      }
+    }
   }
   if (W > 0) {
     SupArgs a{};
@@ -355,6 +469,9 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
     a.W = W;
     a.supA = supA;
     a.supB = supB;
+    a.tbpre = tbpre;
+    a.tb = recs;
+    a.cuv = cuv;
     TR_TRY(launch_walk(0, a, cfg, s));
   }
   k_sum<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, supA, supB, sup, sup64);
@@ -373,6 +490,9 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
   out->wpre = wpre;
   out->walk = W;
   out->entries = total;
+  out->tbpre = recs ? tbpre : nullptr;
+  out->tb = recs;
+  out->cuv = recs ? cuv : nullptr;
   return TRUSS_OK;
 }
 
@@ -380,6 +500,24 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
               cudaStream_t s) {
   const int64_t m = g.m;
   if (m == 0 || so.entries == 0) return TRUSS_OK;
+  if (so.tb) {
+    unsigned long long *cur = A.get<unsigned long long>(m);
+    int *err = A.get<int>(1);
+    if (!cur || !err) return TRUSS_ENOMEM;
+    TR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    k_cursors_rec<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.cuv, cur);
+    TR_LAUNCHED();
+    int dev = 0, sms = cfg.sms;
+    TR_CUDA(cudaGetDevice(&dev));
+    if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    k_lists_from_records<<<sms * 8, 256, 0, s>>>(m, so.tbpre, so.tb, so.cuv, so.toff, cur, pairs,
+                                                 so.entries, err);
+    TR_LAUNCHED();
+    int h_err = 0;
+    TR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaStreamSynchronize(s));
+    return h_err != 0 ? TRUSS_ECHECK : TRUSS_OK;
+  }
   unsigned long long *curA = A.get<unsigned long long>(m), *curB = A.get<unsigned long long>(m);
   int *err = A.get<int>(1);
   if (!curA || !curB || !err) return TRUSS_ENOMEM;
