@@ -279,6 +279,8 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   tr::SupportCfg scfg;
   scfg.sms = ctx->sms;
   scfg.records = want_truss;
+  if (const char *e = getenv("TRUSS_PAIR_COST")) scfg.pair_cost = atoi(e);
+  if (const char *e = getenv("TRUSS_RANGE_WORK")) scfg.range_work = atoll(e);
   tr::SupportOut so;
   TR_TRY(tr::run_support(A, g, scfg, &so, s));
   sg.mark();  // 2

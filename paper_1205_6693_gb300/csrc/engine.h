@@ -101,6 +101,8 @@ struct SupportCfg {
   int block = 256;
   int sms = 0;
   bool records = false;  // also record triangles for the list pass (if memory allows)
+  int pair_cost = 0;      // fixed cost of walking one edge, in out-list entries
+  int64_t range_work = 0; // walk cost per range (0 = default)
 };
 
 // Support of every edge: sup = supA + supB (support.cu).

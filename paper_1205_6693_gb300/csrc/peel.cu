@@ -75,7 +75,7 @@ struct PeelCtl {
   int minres[3];          // per scan (slot = scan index % 3)
   int live[3];            // alive edges left after each scan
   unsigned long long snap[2][2];  // qf, qa at the last two barriers
-  int levels, subrounds, kmax, pad2;
+  int levels, subrounds, kmax, ntrace;
   unsigned long long entries, decrements, scanned;
 };
 
@@ -90,7 +90,7 @@ struct PeelArgs {
   int32_t *alive0, *alive1;
   int4 *Q0, *Q1;      // frontier work items (edge, count | first << 8, offset lo, hi)
   int64_t item_cap;   // capacity of Q0 and Q1
-  int4 *trace;        // optional: per sub-round (k, items, 0, 0)
+  int4 *trace;        // optional: per phase (k, items or -1 for a scan, globaltimer lo/hi)
   int trace_cap;
   PeelCtl *ctl;
   long long wait_ns;
@@ -265,34 +265,41 @@ __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int
   }
 }
 
-// Two triangle entries per lane (all lanes call it; `va`/`vb` mask idle
-// entries).  Each charged triangle decrements its partners outside the
-// frontier; a partner whose residual crosses k-1 -> k-2 joins the next
-// frontier.
-__device__ __forceinline__ void charge2(const PeelArgs &a, int e, bool va, int2 pa, bool vb,
-                                        int2 pb, int k, int s, WarpBuf &wb, int4 *N,
-                                        unsigned long long base_f, unsigned long long &n_dec) {
-  bool a1, a2, b1, b2;
-  decide(a, va, e, pa, s, a1, a2);
-  decide(a, vb, e, pb, s, b1, b2);
-  int o1 = INT_MAX, o2 = INT_MAX, o3 = INT_MAX, o4 = INT_MAX;
-  if (a1) o1 = atomicSub(&a.res[pa.x], 1);
-  if (a2) o2 = atomicSub(&a.res[pa.y], 1);
-  if (b1) o3 = atomicSub(&a.res[pb.x], 1);
-  if (b2) o4 = atomicSub(&a.res[pb.y], 1);
-  n_dec += (unsigned long long)(a1 + a2 + b1 + b2);
-  const bool q1 = o1 == k - 1, q2 = o2 == k - 1, q3 = o3 == k - 1, q4 = o4 == k - 1;
-  if (__any_sync(TR_FULL, q1 || q2 || q3 || q4)) {
-    push_items(a, q1, pa.x, wb, N, base_f, s + 1);
-    push_items(a, q2, pa.y, wb, N, base_f, s + 1);
-    push_items(a, q3, pb.x, wb, N, base_f, s + 1);
-    push_items(a, q4, pb.y, wb, N, base_f, s + 1);
+// NE triangle entries per lane (all lanes call it; `v[i]` masks idle
+// entries, e[i] is the frontier edge of entry i).  Each charged triangle
+// decrements its partners outside the frontier; a partner whose residual
+// crosses k-1 -> k-2 joins the next frontier.  All loads and atomics of the
+// NE entries are issued before any result is used.
+template <int NE>
+__device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bool *v,
+                                       const int2 *p, int k, int s, WarpBuf &wb, int4 *N,
+                                       unsigned long long base_f, unsigned long long &n_dec) {
+  bool d1[NE], d2[NE];
+#pragma unroll
+  for (int i = 0; i < NE; i++) decide(a, v[i], e[i], p[i], s, d1[i], d2[i]);
+  int o1[NE], o2[NE];
+#pragma unroll
+  for (int i = 0; i < NE; i++) {
+    o1[i] = d1[i] ? atomicSub(&a.res[p[i].x], 1) : INT_MAX;
+    o2[i] = d2[i] ? atomicSub(&a.res[p[i].y], 1) : INT_MAX;
+    n_dec += (unsigned long long)(d1[i] + d2[i]);
+  }
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < NE; i++) any |= (o1[i] == k - 1) || (o2[i] == k - 1);
+  if (__any_sync(TR_FULL, any)) {
+#pragma unroll
+    for (int i = 0; i < NE; i++) {
+      push_items(a, o1[i] == k - 1, p[i].x, wb, N, base_f, s + 1);
+      push_items(a, o2[i] == k - 1, p[i].y, wb, N, base_f, s + 1);
+    }
   }
 }
 
 // MINB = resident blocks per SM the register budget is sized for (1: up to
-// 128 registers per thread, 2: 64).
-template <int MINB>
+// 128 registers per thread, 2: 64); G = work items per 8-lane group per
+// iteration (2 entries per lane per item).
+template <int MINB, int G>
 __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   const int lane = lane_id();
   const int wib = threadIdx.x >> 5;
@@ -321,30 +328,42 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
 
   for (;;) {
     // ------------------------------------------------------------ scan ---
+    if (leader && a.trace && ctl->ntrace < a.trace_cap) {
+      const unsigned long long t = global_ns();
+      a.trace[ctl->ntrace++] = make_int4(k, -1, (int)(uint32_t)t, (int)(uint32_t)(t >> 32));
+    }
     const int slot = sc % 3;
     if (leader) {
       ctl->minres[(sc + 1) % 3] = INT_MAX;
       ctl->live[(sc + 1) % 3] = 0;
     }
     int wmin = INT_MAX, wlive = 0;
-    for (int64_t base = gwarp * 32; base < nAlive; base += twarps * 32) {
-      const int64_t i = base + lane;
-      int e = -1, r = 0;
-      bool live = false;
-      if (i < nAlive) {
-        e = __ldcg(&alive[i]);
-        if (__ldcg(&a.stamp[e]) == 0) {
-          live = true;
-          r = __ldcg(&a.res[e]);
-        }
+    // 4 x 32 entries per warp iteration: all loads are issued before any
+    // decision, so one dependent round trip covers 4 entries per lane
+    constexpr int kScanU = 4;
+    for (int64_t base = gwarp * 32 * kScanU; base < nAlive; base += twarps * 32 * kScanU) {
+      int e[kScanU], st[kScanU], r[kScanU];
+#pragma unroll
+      for (int u = 0; u < kScanU; u++) {
+        const int64_t i = base + u * 32 + lane;
+        e[u] = i < nAlive ? __ldcg(&alive[i]) : -1;
       }
-      const bool toF = live && r <= k - 2;
-      const bool keep = live && !toF;
-      push_items(a, toF, e, wb, F, base_f, s);
-      if (compact) push_alive(a, keep, e, wb, alive2, base_a);
-      wmin = min(wmin, __reduce_min_sync(TR_FULL, keep ? r : INT_MAX));
-      wlive += __popc(__ballot_sync(TR_FULL, keep));
-      n_scan += (i < nAlive);
+#pragma unroll
+      for (int u = 0; u < kScanU; u++) {
+        st[u] = e[u] >= 0 ? __ldcg(&a.stamp[e[u]]) : 1;
+        r[u] = e[u] >= 0 ? __ldcg(&a.res[e[u]]) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kScanU; u++) {
+        const bool live = e[u] >= 0 && st[u] == 0;
+        const bool toF = live && r[u] <= k - 2;
+        const bool keep = live && !toF;
+        push_items(a, toF, e[u], wb, F, base_f, s);
+        if (compact) push_alive(a, keep, e[u], wb, alive2, base_a);
+        wmin = min(wmin, __reduce_min_sync(TR_FULL, keep ? r[u] : INT_MAX));
+        wlive += __popc(__ballot_sync(TR_FULL, keep));
+        n_scan += (e[u] >= 0);
+      }
     }
     flush_items(a, wb, F, base_f);
     if (compact) flush_alive(a, wb, alive2, base_a);
@@ -381,31 +400,50 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
     // --------------------------------------------------------- sub-rounds ---
     int64_t nCur = nF;
     for (;;) {
-      if (leader && a.trace && ctl->subrounds < a.trace_cap)
-        a.trace[ctl->subrounds] = make_int4(k, (int)min(nCur, (int64_t)INT_MAX), 0, 0);
+      if (leader && a.trace && ctl->ntrace < a.trace_cap) {
+        const unsigned long long t = global_ns();
+        a.trace[ctl->ntrace++] = make_int4(k, (int)min(nCur, (int64_t)INT_MAX),
+                                           (int)(uint32_t)t, (int)(uint32_t)(t >> 32));
+      }
       const int grp = lane >> 3, j = lane & 7;
-      for (int64_t base = gwarp * 4; base < nCur; base += twarps * 4) {
-        const int64_t it = base + grp;
-        int e = 0, cnt = 0;
-        int64_t lb = 0;
-        if (it < nCur) {
-          const int4 item = __ldcg(&F[it]);
-          e = item.x;
-          cnt = item.y & 0xFF;
-          lb = (int64_t)(((uint64_t)(uint32_t)item.w << 32) | (uint32_t)item.z);
-          if ((item.y >> 8) && j == 0) a.truss[e] = k;
+      for (int64_t base = gwarp * 4 * G; base < nCur; base += twarps * 4 * G) {
+        int ee[2 * G];
+        bool vv[2 * G];
+        int2 pp[2 * G];
+        int cnt[G];
+        int64_t lb[G];
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          const int64_t it = base + g * 4 + grp;
+          ee[2 * g] = 0;
+          cnt[g] = 0;
+          lb[g] = 0;
+          if (it < nCur) {
+            const int4 item = __ldcg(&F[it]);
+            ee[2 * g] = item.x;
+            cnt[g] = item.y & 0xFF;
+            lb[g] = (int64_t)(((uint64_t)(uint32_t)item.w << 32) | (uint32_t)item.z);
+            if ((item.y >> 8) && j == 0) a.truss[item.x] = k;
+          }
+          ee[2 * g + 1] = ee[2 * g];
         }
-        const bool ha = j < cnt, hb = j + 8 < cnt;
-        int2 pa = make_int2(0, 0), pb = make_int2(0, 0);
-        int r = 0;
-        if (ha) {
-          r = __ldcg(&a.res[e]);
-          pa = __ldg(&a.pairs[lb + j]);
+        int r[G];
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          const bool ha = j < cnt[g], hb = j + 8 < cnt[g];
+          r[g] = ha ? __ldcg(&a.res[ee[2 * g]]) : 0;
+          pp[2 * g] = ha ? __ldg(&a.pairs[lb[g] + j]) : make_int2(0, 0);
+          pp[2 * g + 1] = hb ? __ldg(&a.pairs[lb[g] + j + 8]) : make_int2(0, 0);
+          vv[2 * g] = ha;
+          vv[2 * g + 1] = hb;
         }
-        if (hb) pb = __ldg(&a.pairs[lb + j + 8]);
-        const bool va = ha && r > 0, vb = hb && r > 0;
-        n_entries += (unsigned long long)(va + vb);
-        charge2(a, e, va, pa, vb, pb, k, s, wb, N, base_f, n_dec);
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          vv[2 * g] = vv[2 * g] && r[g] > 0;
+          vv[2 * g + 1] = vv[2 * g + 1] && r[g] > 0;
+          n_entries += (unsigned long long)(vv[2 * g] + vv[2 * g + 1]);
+        }
+        charge<2 * G>(a, ee, vv, pp, k, s, wb, N, base_f, n_dec);
       }
       flush_items(a, wb, N, base_f);
       if (!grid_barrier(ctl, a.wait_ns, snap)) return;
@@ -423,6 +461,10 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
       ctl->kmax = k;
     }
     k++;
+  }
+  if (leader && a.trace && ctl->ntrace < a.trace_cap) {
+    const unsigned long long t = global_ns();
+    a.trace[ctl->ntrace++] = make_int4(k, -2, (int)(uint32_t)t, (int)(uint32_t)(t >> 32));
   }
   // totals (one atomic per warp)
   for (int o = 16; o >= 1; o >>= 1) {
@@ -474,16 +516,22 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
   int dev = 0, sms = cfg.sms;
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const bool one = cfg.blocks_per_sm == 1;
-  const void *kern = one ? (const void *)k_peel<1> : (const void *)k_peel<2>;
+  // blocks_per_sm 1: 128-register variant taking 2 items per lane group;
+  // otherwise the 64-register variant with 1 item per group (3: 1 item,
+  // 1 block per SM)
+  const int variant = cfg.blocks_per_sm == 1 ? 1 : (cfg.blocks_per_sm == 3 ? 3 : 2);
+  const void *kern = variant == 1 ? (const void *)k_peel<1, 2>
+                     : variant == 3 ? (const void *)k_peel<1, 1> : (const void *)k_peel<2, 1>;
   int occ = 0;
-  if (one) {
-    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<1>, kPeelBlock, 0));
+  if (variant == 1) {
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<1, 2>, kPeelBlock, 0));
+  } else if (variant == 3) {
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<1, 1>, kPeelBlock, 0));
   } else {
-    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<2>, kPeelBlock, 0));
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<2, 1>, kPeelBlock, 0));
   }
   if (occ < 1) return TRUSS_ECUDA;
-  if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < occ) occ = cfg.blocks_per_sm;
+  if (variant != 2 && occ > 1) occ = 1;
   PeelArgs a{};
   a.m = m;
   a.toff = so.toff;
@@ -519,12 +567,14 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
   out->decrements = h.decrements;
   out->scanned = h.scanned;
   if (trace_path && a.trace) {
-    const int nsub = h.subrounds < trace_cap ? h.subrounds : trace_cap;
-    std::vector<int4> t((size_t)nsub);
-    TR_CUDA(cudaMemcpy(t.data(), a.trace, sizeof(int4) * nsub, cudaMemcpyDeviceToHost));
+    const int nt = h.ntrace < trace_cap ? h.ntrace : trace_cap;
+    std::vector<int4> t((size_t)nt);
+    TR_CUDA(cudaMemcpy(t.data(), a.trace, sizeof(int4) * nt, cudaMemcpyDeviceToHost));
     if (FILE *f = fopen(trace_path, "w")) {
-      fprintf(f, "k,items\n");
-      for (auto &x : t) fprintf(f, "%d,%d\n", x.x, x.y);
+      fprintf(f, "k,items,t_ns\n");  // items: -1 = level scan, -2 = end
+      for (auto &x : t)
+        fprintf(f, "%d,%d,%llu\n", x.x, x.y,
+                ((unsigned long long)(uint32_t)x.w << 32) | (uint32_t)x.z);
       fclose(f);
     }
   }

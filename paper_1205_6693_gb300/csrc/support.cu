@@ -85,14 +85,15 @@ __device__ __forceinline__ int64_t lower_bound64(const int64_t *a, int64_t m, in
   return lo;
 }
 
-// Out-list of u as seen by one warp: staged in shared memory or read from
-// global memory.
+// Out-list of u as seen by one warp: staged in shared memory (STAGED) or
+// read from global memory.  A compile-time choice, so the staged case
+// compiles to plain shared-memory loads.
+template <bool STAGED>
 struct OutList {
   const int32_t *L;
   int d;
-  bool staged;
 
-  __device__ __forceinline__ int at(int i) const { return staged ? L[i] : __ldg(&L[i]); }
+  __device__ __forceinline__ int at(int i) const { return STAGED ? L[i] : __ldg(&L[i]); }
 
   // Lower bound of w in L[lo, d): a branch-free search whose step count
   // depends only on d - lo, which is the same for every lane of the warp.
@@ -151,9 +152,9 @@ __device__ __forceinline__ void found(const SupArgs &a, int64_t bu, void *Cv, in
 // merged order (A first on ties), finds its start by a binary search on its
 // diagonal and then merges K steps; an A entry equal to the current B head
 // is a triangle.
-template <int MODE>
-__device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList &ol, void *Cv,
-                                     int i0, int i1, int32_t *Abuf, int *uvc) {
+template <int MODE, bool STAGED>
+__device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList<STAGED> &ol,
+                                     void *Cv, int i0, int i1, int32_t *Abuf, int *uvc) {
   const int lane = lane_id();
   const int d = ol.d;
   const int Lmax = ol.at(d - 1);
@@ -250,27 +251,26 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
       const int i1 = min(iend, d - 1);  // the last out-neighbour closes no triangle here
       if (i0 >= i1) continue;
       const bool whole = i0 == 0 && iend >= d - 1;  // this warp walks all of out(u)
-      OutList ol;
-      ol.d = d;
-      ol.staged = d <= CAP;
+      const bool staged = d <= CAP;
       void *C;
-      if (ol.staged) {
+      if (staged) {
         for (int q = lane; q < d; q += 32) {
           Ls[q] = __ldg(&a.adjp[bu + q]);
           if (MODE == 0) ((int32_t *)Cs)[q] = 0;
           else ((unsigned long long *)Cs)[q] = (unsigned long long)__ldg(&a.curA[bu + q]);
         }
         __syncwarp();
-        ol.L = Ls;
         C = Cs;
         if (MODE == 1 && !whole) C = a.curA + bu;  // cursors shared by several ranges
+        OutList<true> ol{Ls, d};
+        walk<MODE, true>(a, bu, ol, C, i0, i1, Abuf, uvc);
       } else {
-        ol.L = a.adjp + bu;
         C = MODE == 0 ? (void *)(a.supA + bu) : (void *)(a.curA + bu);
+        OutList<false> ol{a.adjp + bu, d};
+        walk<MODE, false>(a, bu, ol, C, i0, i1, Abuf, uvc);
       }
-      walk<MODE>(a, bu, ol, C, i0, i1, Abuf, uvc);
       __syncwarp();
-      if (MODE == 0 && ol.staged) {
+      if (MODE == 0 && staged) {
         const int32_t *Ci = (const int32_t *)Cs;
         for (int q = lane; q < d; q += 32) {
           if (whole) a.supA[bu + q] = Ci[q];
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
 // entry of out(u); and the most triangles (u, v, w) it can close,
 // min(|out(v)|, entries of out(u) after v).
 __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
-                            const int32_t *esrc, int64_t *cost, int64_t *bound) {
+                            const int32_t *esrc, int64_t *cost, int64_t *bound, int pair_cost) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t c = 0, b = 0;
@@ -295,8 +295,9 @@ __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
       const int64_t end = offp[u + 1];
       if (e != end - 1) {
         const int v = adjp[e];
-        c = offp[v + 1] - offp[v];
-        b = min(c, end - 1 - e);
+        const int64_t a = offp[v + 1] - offp[v];
+        b = min(a, end - 1 - e);
+        c = a + pair_cost;
       }
     }
     cost[e] = c;
@@ -397,7 +398,7 @@ int launch_walk(int mode, SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
   if (occ < 1) occ = 1;
   const int grid = sms * occ;
   const int64_t warps = (int64_t)grid * (kBlock / 32);
-  int64_t P = a.W / kRangeWork;
+  int64_t P = a.W / (cfg.range_work > 0 ? cfg.range_work : kRangeWork);
   if (P < warps) P = warps;
   if (P > a.m) P = a.m > 0 ? a.m : 1;
   a.P = P;
@@ -422,7 +423,7 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
   int64_t W = 0, R = 0;
   if (m > 0) {
     k_walk_cost<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, g.offp, g.adjp, g.esrc, wcost,
-                                                                wbound);
+                                                                wbound, cfg.pair_cost);
     TR_LAUNCHED();
     size_t tb = 0;
     TR_TRY(exclusive_sum_i64(nullptr, &tb, wcost, wpre, m + 1, s));
