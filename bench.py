@@ -62,6 +62,39 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def csrc_sha256() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1205_6693_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_for(stage: str):
+    """DRAM bytes per launch of `stage`'s kernel from the committed ncu
+    capture, or None if the CUDA sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic_mid_rmat20.txt")
+    if not os.path.exists(path):
+        return None
+    sha, rows = None, {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if parts[0] == "csrc_sha256":
+                sha = parts[1]
+            elif len(parts) >= 4:
+                rows[parts[0]] = int(parts[2]) + int(parts[3])
+    if sha != csrc_sha256():
+        return None
+    return rows.get(stage)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -447,12 +480,7 @@ def main():
     kernel_name = {"support": "k_support<0>",
                    "lists": "k_support<1>",
                    "peel": "k_peel (persistent, cooperative)"}[dom]
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        with open(tfile) as f:
-            tj = json.load(f)
-        traffic = tj.get(dom)
+    traffic = traffic_for(dom)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:

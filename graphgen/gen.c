@@ -329,3 +329,85 @@ void gg_serve_schedule(int64_t count, double lambda, double mlo, double mhi, uin
     m[j] = (int64_t)floor(gg_exp(lm) + 0.5);
   }
 }
+
+/* ------------------------------------------- first-m-distinct by sorting --- */
+/* Same rows as gg_chung_lu (the first m distinct non-loop pairs of the
+ * sample stream, in sample order), found by sorting instead of a hash set:
+ * draw S samples, sort (pair key, sample index) with a stable LSD radix sort,
+ * keep the first index of every key, then emit the first m kept samples in
+ * sample order.  If S samples hold fewer than m distinct pairs, S grows. */
+static void radix_sort_u64_idx(uint64_t *key, uint32_t *idx, uint64_t *tk, uint32_t *ti,
+                               int64_t n, int bits) {
+  enum { R = 11 };
+  static int64_t cnt[1 << R];
+  uint64_t *k0 = key, *k1 = tk;
+  uint32_t *i0 = idx, *i1 = ti;
+  const uint64_t mask = (1ull << R) - 1;
+  for (int shift = 0; shift < bits; shift += R) {
+    memset(cnt, 0, sizeof(cnt));
+    for (int64_t i = 0; i < n; i++) cnt[(k0[i] >> shift) & mask]++;
+    int64_t sum = 0;
+    for (int b = 0; b < (1 << R); b++) {
+      const int64_t c = cnt[b];
+      cnt[b] = sum;
+      sum += c;
+    }
+    for (int64_t i = 0; i < n; i++) {
+      const int64_t p = cnt[(k0[i] >> shift) & mask]++;
+      k1[p] = k0[i];
+      i1[p] = i0[i];
+    }
+    uint64_t *tkp = k0; k0 = k1; k1 = tkp;   /* the sorted data is now in k0/i0 */
+    uint32_t *tip = i0; i0 = i1; i1 = tip;
+  }
+  if (k0 != key) {
+    memcpy(key, k0, sizeof(uint64_t) * (size_t)n);
+    memcpy(idx, i0, sizeof(uint32_t) * (size_t)n);
+  }
+}
+
+int64_t gg_chung_lu_sorted(int64_t n, int64_t m, const uint64_t *thr, const int32_t *alias,
+                           uint64_t seed, uint64_t stream, int32_t *src, int32_t *dst) {
+  uint64_t key0 = sm_key(seed, stream);
+  int bits = 1;
+  while (bits < 64 && ((uint64_t)1 << bits) < (uint64_t)n) bits++;
+  int64_t S = m + m / 16 + 1024;
+  for (;;) {
+    if (S > 0xFFFFFFFFll) return -1;
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)S);
+    uint64_t *tk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)S);
+    uint32_t *idx = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)S);
+    uint32_t *ti = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)S);
+    unsigned char *first = (unsigned char *)calloc((size_t)S, 1);
+    if (!key || !tk || !idx || !ti || !first) {
+      free(key); free(tk); free(idx); free(ti); free(first);
+      return -1;
+    }
+    const uint64_t loop = ~0ull;
+    for (int64_t c = 0; c < S; c++) {
+      uint32_t u = alias_pick(sm_at(key0, 2 * (uint64_t)c), n, thr, alias);
+      uint32_t v = alias_pick(sm_at(key0, 2 * (uint64_t)c + 1), n, thr, alias);
+      key[c] = u == v ? loop : (((uint64_t)(u < v ? u : v) << bits) | (u < v ? v : u));
+      idx[c] = (uint32_t)c;
+    }
+    radix_sort_u64_idx(key, idx, tk, ti, S, 64);
+    int64_t distinct = 0;
+    for (int64_t i = 0; i < S; i++) {
+      if (key[i] == loop) continue;
+      if (i == 0 || key[i] != key[i - 1]) { first[idx[i]] = 1; distinct++; }
+    }
+    if (distinct >= m) {
+      int64_t k = 0;
+      for (int64_t c = 0; c < S && k < m; c++) {
+        if (!first[c]) continue;
+        src[k] = (int32_t)alias_pick(sm_at(key0, 2 * (uint64_t)c), n, thr, alias);
+        dst[k] = (int32_t)alias_pick(sm_at(key0, 2 * (uint64_t)c + 1), n, thr, alias);
+        k++;
+      }
+      free(key); free(tk); free(idx); free(ti); free(first);
+      return k;
+    }
+    free(key); free(tk); free(idx); free(ti); free(first);
+    S = S + S / 2;
+  }
+}

@@ -91,3 +91,12 @@ def test_generator_is_deterministic():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     n, s, d = graphgen.tiny()
     assert len(s) == 33942 and n == 4096
+
+
+def test_chung_lu_sorted_selection_equals_hash_set_selection():
+    import numpy as np
+    import graphgen
+    for n, m, cap, seed in [(5000, 40000, 500.0, 1), (30000, 300000, 3000.0, 2)]:
+        a = graphgen.chung_lu(n, m, 20.0, cap, 2.1, seed=seed)
+        b = graphgen.chung_lu(n, m, 20.0, cap, 2.1, seed=seed, sorted_dedup=True)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
