@@ -50,6 +50,9 @@ def _L():
         L.oracle_edges.restype = ctypes.c_int
         L.oracle_edges.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p, _i32p,
                                    _i32p, _i64p]
+        L.oracle_check_sample.restype = ctypes.c_int64
+        L.oracle_check_sample.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p,
+                                          _i32p, ctypes.c_int64, _i64p, _i32p]
         L.oracle_check_valid.restype = ctypes.c_int64
         L.oracle_check_valid.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p,
                                          _i32p]
@@ -115,3 +118,20 @@ def check_valid(n: int, src, dst, truss_rows, support_rows) -> int:
     return int(_L().oracle_check_valid(n, len(src), src.ctypes.data_as(_i32p),
                                        dst.ctypes.data_as(_i32p), t.ctypes.data_as(_i32p),
                                        s.ctypes.data_as(_i32p)))
+
+
+def check_sample(n: int, src, dst, truss_rows, support_rows, sample_rows):
+    """Per sampled row: exact support by neighbour-list intersection and local
+    validity of the claimed truss number (see alg2.c).  Returns (violations,
+    exact supports of the sampled rows)."""
+    src, dst = _c(src), _c(dst)
+    t, s = _c(truss_rows), _c(support_rows)
+    smp = np.ascontiguousarray(sample_rows, dtype=np.int64)
+    out = np.empty(max(len(smp), 1), np.int32)
+    bad = _L().oracle_check_sample(n, len(src), src.ctypes.data_as(_i32p),
+                                   dst.ctypes.data_as(_i32p), t.ctypes.data_as(_i32p),
+                                   s.ctypes.data_as(_i32p), len(smp),
+                                   smp.ctypes.data_as(_i64p), out.ctypes.data_as(_i32p))
+    if bad < 0:
+        raise ValueError("oracle_check_sample failed")
+    return int(bad), out[:len(smp)]

@@ -356,3 +356,46 @@ int64_t oracle_check_valid(int64_t n, int64_t rows, const int32_t *src, const in
   g_free(&g);
   return bad;
 }
+
+/* Sampled check of a claimed result at any size (Definitions 1 and 2): for
+ * each sampled row r (not a self-loop) with edge e = (u, v), its support is
+ * |nb(u) cap nb(v)| (merge of the two sorted lists), and e must lie in
+ * >= phi(e) - 2 triangles whose other two edges have phi >= phi(e); phi = 2
+ * iff the support is 0.  Writes the exact support of each sampled row to
+ * sup_sample and returns the number of sampled rows violating any check. */
+int64_t oracle_check_sample(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+                            const int32_t *truss_rows, const int32_t *support_rows,
+                            int64_t ns, const int64_t *sample, int32_t *sup_sample) {
+  graph g;
+  if (g_build(&g, n, rows, src, dst)) { g_free(&g); return -1; }
+  int32_t *phi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g.m + 1));
+  for (int64_t r = 0; r < rows; r++)
+    if (g.row2e[r] >= 0) phi[g.row2e[r]] = truss_rows[r];
+  int64_t bad = 0;
+  for (int64_t t = 0; t < ns; t++) {
+    const int64_t r = sample[t];
+    const int32_t e = g.row2e[r];
+    if (e < 0) { sup_sample[t] = -1; bad += truss_rows[r] != -1 || support_rows[r] != -1; continue; }
+    const int32_t u = g.eu[e], v = g.ev[e];
+    const int32_t pe = truss_rows[r];  /* the sampled row's own claim */
+    int64_t i = g.off[u], j = g.off[v];
+    int32_t sup = 0, in = 0;
+    while (i < g.off[u + 1] && j < g.off[v + 1]) {
+      const int32_t a = g.adj[i], b = g.adj[j];
+      if (a < b) i++;
+      else if (a > b) j++;
+      else {
+        sup++;
+        if (phi[g.adje[i]] >= pe && phi[g.adje[j]] >= pe) in++;
+        i++; j++;
+      }
+    }
+    sup_sample[t] = sup;
+    const int ok = support_rows[r] == sup && pe >= 2 && pe <= sup + 2 && in >= pe - 2 &&
+                   ((pe == 2) == (sup == 0)) && phi[e] == pe;  /* duplicates agree */
+    bad += !ok;
+  }
+  free(phi);
+  g_free(&g);
+  return bad;
+}

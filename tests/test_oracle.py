@@ -274,3 +274,20 @@ def test_tiny_config_planted_cliques():
         base += s
         assert all(key[e] >= s for e in clique(vs))
     assert r.kmax == 32
+
+
+def test_sampled_checker_accepts_oracle_and_rejects_mistakes():
+    n, (src, dst) = 2 ** 12, graphgen.rmat_raw(12, 16 * 2 ** 12, seed=21)
+    r = oracle.truss(n, src, dst)
+    sample = np.arange(0, len(src), 7, dtype=np.int64)
+    bad, sup = oracle.check_sample(n, src, dst, r.truss, r.support, sample)
+    assert bad == 0 and np.array_equal(sup, r.support[sample])
+    t = r.truss.copy()
+    i = int(np.argmax(t))
+    t[i] += 1  # too high a truss number is not locally valid
+    bad, _ = oracle.check_sample(n, src, dst, t, r.support, np.array([i], np.int64))
+    assert bad == 1
+    s = r.support.copy()
+    s[sample[3]] += 1
+    bad, _ = oracle.check_sample(n, src, dst, r.truss, s, sample)
+    assert bad == 1
