@@ -218,6 +218,18 @@ def _max_over_ranks(dist, dev, x: float) -> float:
     return float(t.item())
 
 
+def schedule_for(args, local, rows, graphs, call):
+    """Schedule opts for this GPU and size bucket: from the autotuner's cache,
+    else tuned now (untimed, before the warm-up), else the defaults."""
+    from paper_1205_6693_gb300 import autotune
+    got = autotune.lookup(autotune.gpu_key(local), rows, graphs, nearest=False)
+    if got is not None:
+        return got, "cache"
+    if args.no_tune:
+        return {}, "default"
+    return autotune.tune_call(local, call, rows, graphs)["opts"], "tuned"
+
+
 def run_batch(args, ws, rank, local):
     """Batched form: the mixed 4,096-graph batch in one truss_decompose_batch
     call, against per-graph truss_decompose calls on the same stream."""
@@ -235,7 +247,10 @@ def run_batch(args, ws, rank, local):
     kmax = torch.empty(G, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    ctx = T.Context(local, profile=True)
+    sched, sched_src = schedule_for(
+        args, local, int(off[-1]), G,
+        lambda c: (c.decompose_batch(ns, off, src, dst, sup, tr, kmax), (sup, tr, kmax))[1])
+    ctx = T.Context(local, profile=True, **sched)
     for _ in range(args.warmup):
         ctx.decompose_batch(ns, off, src, dst, sup, tr, kmax, stream=stream)
     torch.cuda.synchronize(dev)
@@ -276,7 +291,8 @@ def run_batch(args, ws, rank, local):
                            "rows": int(off[-1]) * ws, "edges_rank0": st["m"],
                            "triangles_rank0": st["triangles"],
                            "parallelism": f"graphs sharded over {ws} rank(s)",
-                           "l2_flush": True},
+                           "l2_flush": True,
+                           "schedule": {"opts": sched, "source": sched_src}},
                 "per_graph_loop": {"value": args.graphs / (loop_ms / 1e3), "unit": "graphs/s",
                                    "ms": loop_ms},
                 "speedup_vs_loop": (args.graphs * args.steps / (ms / 1e3))
@@ -369,6 +385,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use cached or default schedules; never run the autotuner")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
     ap.add_argument("--graphs", type=int, default=4096, help="batch mode: graphs")
     ap.add_argument("--window", type=float, default=1.0, help="serve mode: arrival window (s)")
@@ -407,7 +425,9 @@ def main():
     counts = cctx.stats()
     cctx.close()
 
-    ctx = T.Context(local, profile=True)
+    sched, sched_src = schedule_for(
+        args, local, rows, 1, lambda c: (c.decompose(n, src, dst, sup, tr), (sup, tr))[1])
+    ctx = T.Context(local, profile=True, **sched)
     for _ in range(max(args.warmup, 0)):
         ctx.decompose(n, src, dst, sup, tr)
     torch.cuda.synchronize(dev)
@@ -478,7 +498,7 @@ def main():
     dms, dbytes = cand[dom]
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
     kernel_name = {"support": "k_support<0>",
-                   "lists": "k_support<1>",
+                   "lists": "k_lists_from_records",
                    "peel": "k_peel (persistent, cooperative)"}[dom]
     traffic = traffic_for(dom)
 
@@ -496,7 +516,8 @@ def main():
         "config": {"workload": WORKLOAD, "m": m, "rows": rows, "triangles": st["triangles"],
                    "kmax": kmax, "parallelism": f"replicas x{ws}", "l2_flush": True,
                    "stage_ms_median": {k: round(v, 3) for k, v in med.items()},
-                   "levels": st["levels"], "subrounds": st["subrounds"]},
+                   "levels": st["levels"], "subrounds": st["subrounds"],
+                   "schedule": {"opts": sched, "source": sched_src}},
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes": dbytes},

@@ -72,21 +72,35 @@ typedef struct truss_opts {
   /* Non-zero: also compute the algorithmic byte counts of the support and
    * peel kernels (one extra host pass over small arrays). */
   int32_t count_bytes;
-  /* Threads per block of the support/list kernels (0 = tuned default). */
-  int32_t support_block;
-  /* Resident blocks per SM of the persistent peel kernel (0 = occupancy max). */
-  int32_t peel_blocks_per_sm;
-  /* Frontier size at or below which the peel runs a level's sub-rounds inside
-   * one block (block barriers instead of grid barriers).  <0 disables, 0 =
-   * tuned default. */
-  int32_t peel_small_frontier;
-  int32_t reserved[8];
+  /* The fields below choose schedules only: every value gives the same
+   * outputs.  0 selects the built-in default for each. */
+  /* Hub threshold of the support walk: out-lists of at most this many
+   * entries are staged in shared memory, longer ones are read from global
+   * memory (0 = the staging capacity, 512; larger values are clamped). */
+  int32_t support_stage_max;
+  /* Peel kernel variant: 0 or 2 = two 512-thread blocks per SM, one work item
+   * per lane group; 1 = one block per SM, two items per lane group; 3 = one
+   * block per SM, one item. */
+  int32_t peel_variant;
+  /* Target walk cost (out-list entries) of one warp range of the support
+   * walk (0 = 16384). */
+  int32_t support_range_work;
+  /* Fixed cost, in out-list entries, added per walked edge when the support
+   * walk is split into equal-cost ranges (0 = none). */
+  int32_t support_pair_cost;
+  int32_t reserved[7];
 } truss_opts;
 
 /* Create a context bound to CUDA device `device` (ordinal).  opts may be NULL
  * (all defaults).  *out receives the context.  Errors: TRUSS_EINVAL (bad
  * device or NULL out), TRUSS_ECUDA, TRUSS_ENOMEM. */
 int truss_ctx_create(truss_ctx **out, int device, const truss_opts *opts);
+
+/* Replace the options of an existing context; they apply from its next call
+ * (the workspace is kept).  The library has no counterpart in the paper: it
+ * lets a schedule search time candidates on one warm context.  Errors:
+ * TRUSS_EINVAL (NULL ctx or opts). */
+int truss_ctx_set_opts(truss_ctx *ctx, const truss_opts *opts);
 
 /* Release the context and its workspace.  NULL is accepted. */
 int truss_ctx_destroy(truss_ctx *ctx);

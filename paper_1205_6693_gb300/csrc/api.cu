@@ -279,8 +279,9 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   tr::SupportCfg scfg;
   scfg.sms = ctx->sms;
   scfg.records = want_truss;
-  if (const char *e = getenv("TRUSS_PAIR_COST")) scfg.pair_cost = atoi(e);
-  if (const char *e = getenv("TRUSS_RANGE_WORK")) scfg.range_work = atoll(e);
+  scfg.pair_cost = ctx->opts.support_pair_cost;
+  scfg.range_work = ctx->opts.support_range_work;
+  scfg.stage_max = ctx->opts.support_stage_max;
   tr::SupportOut so;
   TR_TRY(tr::run_support(A, g, scfg, &so, s));
   sg.mark();  // 2
@@ -310,8 +311,7 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
     sg.mark();  // 3
     tr::PeelCfg pcfg;
     pcfg.sms = ctx->sms;
-    pcfg.blocks_per_sm = ctx->opts.peel_blocks_per_sm;
-    pcfg.small_frontier = ctx->opts.peel_small_frontier;
+    pcfg.variant = ctx->opts.peel_variant;
     if (ctx->opts.wait_limit_ns > 0) pcfg.wait_ns = ctx->opts.wait_limit_ns;
     int rc = tr::run_peel(A, g, so, pairs, pcfg, truss_e, &pr, s);
     if (rc != TRUSS_OK) return rc;
@@ -361,7 +361,7 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   st.launches = tr::take_launches();
   if (ctx->opts.count_bytes) {
     double bs = 0, bl = 0;
-    TR_TRY(tr::count_support_bytes(A, g, st.triangles, &bs, &bl, s));
+    TR_TRY(tr::count_support_bytes(A, g, st.triangles, so.tb != nullptr, &bs, &bl, s));
     st.bytes_support = bs;
     st.bytes_lists = want_truss ? bl : 0.0;
     if (want_truss)
@@ -455,6 +455,12 @@ int truss_ctx_create(truss_ctx **out, int device, const truss_opts *opts) {
   for (auto &e : c->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
   c->have_events = ok;
   *out = c;
+  return TRUSS_OK;
+}
+
+int truss_ctx_set_opts(truss_ctx *ctx, const truss_opts *opts) {
+  if (!ctx || !opts) return TRUSS_EINVAL;
+  ctx->opts = *opts;
   return TRUSS_OK;
 }
 

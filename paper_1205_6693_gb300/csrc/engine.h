@@ -103,6 +103,7 @@ struct SupportCfg {
   bool records = false;  // also record triangles for the list pass (if memory allows)
   int pair_cost = 0;      // fixed cost of walking one edge, in out-list entries
   int64_t range_work = 0; // walk cost per range (0 = default)
+  int stage_max = 0;      // stage out-lists of at most this many entries (0 = capacity)
 };
 
 // Support of every edge: sup = supA + supB (support.cu).
@@ -115,9 +116,8 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
 // ---------------------------------------------------------------- peel ---
 struct PeelCfg {
   int block = 512;
-  int blocks_per_sm = 0;
+  int variant = 0;  // kernel shape (peel.cu: run_peel)
   int sms = 0;
-  int small_frontier = 0;
   long long wait_ns = 4000000000LL;
 };
 
@@ -140,7 +140,7 @@ int batch_graph_counts(const Csr &g, int32_t G, const int64_t *voff, const int32
                        unsigned long long *m_g, unsigned long long *sup_g, cudaStream_t s);
 
 // Algorithmic byte counts (see the comments in support.cu / peel.cu).
-int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, double *b_sup,
+int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, double *b_sup,
                         double *b_lists, cudaStream_t s);
 
 }  // namespace tr

@@ -516,10 +516,10 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
   int dev = 0, sms = cfg.sms;
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // blocks_per_sm 1: 128-register variant taking 2 items per lane group;
-  // otherwise the 64-register variant with 1 item per group (3: 1 item,
-  // 1 block per SM)
-  const int variant = cfg.blocks_per_sm == 1 ? 1 : (cfg.blocks_per_sm == 3 ? 3 : 2);
+  // variant 1: 128-register kernel taking 2 items per lane group, one block
+  // per SM; 3: 1 item per group, one block per SM; otherwise (0, 2) the
+  // 64-register kernel with 1 item per group and two blocks per SM
+  const int variant = cfg.variant == 1 ? 1 : (cfg.variant == 3 ? 3 : 2);
   const void *kern = variant == 1 ? (const void *)k_peel<1, 2>
                      : variant == 3 ? (const void *)k_peel<1, 1> : (const void *)k_peel<2, 1>;
   int occ = 0;

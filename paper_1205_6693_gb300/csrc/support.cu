@@ -61,6 +61,7 @@ struct SupArgs {
   const int64_t *wpre;  // [m+1] exclusive prefix of the walk cost per edge
   int64_t W;            // total walk cost
   int64_t P;            // number of ranges
+  int stage_max;        // stage out(u) in shared memory when |out(u)| <= this
   int32_t *supA;        // MODE 0: owner counts; MODE 1: read
   int32_t *supB;        // MODE 0: (v, w)-edge counts
   unsigned long long *curA;  // MODE 1: next slot of e's owner part (starts at toff[e])
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
       const int i1 = min(iend, d - 1);  // the last out-neighbour closes no triangle here
       if (i0 >= i1) continue;
       const bool whole = i0 == 0 && iend >= d - 1;  // this warp walks all of out(u)
-      const bool staged = d <= CAP;
+      const bool staged = d <= a.stage_max;
       void *C;
       if (staged) {
         for (int q = lane; q < d; q += 32) {
@@ -402,6 +403,8 @@ int launch_walk(int mode, SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
   if (P < warps) P = warps;
   if (P > a.m) P = a.m > 0 ? a.m : 1;
   a.P = P;
+  const int cap = mode == 0 ? Cap<0>::value : Cap<1>::value;
+  a.stage_max = cfg.stage_max > 0 && cfg.stage_max < cap ? cfg.stage_max : cap;
   if (mode == 0) k_support<0><<<grid, kBlock, smem, s>>>(a);
   else k_support<1><<<grid, kBlock, smem, s>>>(a);
   TR_LAUNCHED();
@@ -577,7 +580,7 @@ __global__ void k_count_walk(int64_t n, const int64_t *offp, const int32_t *adjp
 // read-modify-write of supB).  Of the list pass: walk bytes + 60 B per
 // triangle (three 8-B list entries written, three 8-B list offsets and one
 // 4-B owner count read, one 8-B cursor read-modify-write).
-int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, double *b_sup,
+int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, double *b_sup,
                         double *b_lists, cudaStream_t s) {
   unsigned long long *acc = A.get<unsigned long long>(1);
   if (!acc) return TRUSS_ENOMEM;
@@ -589,8 +592,11 @@ int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, double *b_sup
   unsigned long long h = 0;
   TR_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
   TR_CUDA(cudaStreamSynchronize(s));
-  *b_sup = (double)h + 8.0 * (double)triangles;
-  *b_lists = (double)h + 60.0 * (double)triangles;
+  // per triangle: the (v, w) count RMW, plus the 8-B record when recording;
+  // lists from records: record read, three entries, two cursor RMWs (48 B);
+  // lists by a second walk: the walk again plus 60 B per triangle
+  *b_sup = (double)h + (records ? 16.0 : 8.0) * (double)triangles;
+  *b_lists = records ? 48.0 * (double)triangles : (double)h + 60.0 * (double)triangles;
   return TRUSS_OK;
 }
 

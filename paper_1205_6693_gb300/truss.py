@@ -39,9 +39,9 @@ class TrussError(RuntimeError):
 
 class truss_opts(ctypes.Structure):
     _fields_ = [("wait_limit_ns", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("count_bytes", ctypes.c_int32), ("support_block", ctypes.c_int32),
-                ("peel_blocks_per_sm", ctypes.c_int32), ("peel_small_frontier", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("count_bytes", ctypes.c_int32), ("support_stage_max", ctypes.c_int32),
+                ("peel_variant", ctypes.c_int32), ("support_range_work", ctypes.c_int32),
+                ("support_pair_cost", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class truss_run_stats(ctypes.Structure):
@@ -94,7 +94,8 @@ _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
 
 # Symbols declared in include/truss.h (checked by the CPU test suite).
-EXPORTS = ("truss_strerror", "truss_ctx_create", "truss_ctx_destroy", "truss_support",
+EXPORTS = ("truss_strerror", "truss_ctx_create", "truss_ctx_set_opts", "truss_ctx_destroy",
+           "truss_support",
            "truss_decompose", "truss_decompose_batch", "truss_last_stats",
            "truss_serve_footprint", "truss_serve_start", "truss_serve_submit", "truss_serve_poll",
            "truss_serve_wait", "truss_serve_stop", "truss_support_noalloc")
@@ -120,6 +121,8 @@ def _lib():
                                        ctypes.POINTER(truss_opts)]
         L.truss_ctx_destroy.restype = ctypes.c_int
         L.truss_ctx_destroy.argtypes = [_vp]
+        L.truss_ctx_set_opts.restype = ctypes.c_int
+        L.truss_ctx_set_opts.argtypes = [_vp, ctypes.POINTER(truss_opts)]
         L.truss_support.restype = ctypes.c_int
         L.truss_support.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp]
         L.truss_decompose.restype = ctypes.c_int
@@ -200,6 +203,10 @@ def truss_ctx_create(device: int = 0, opts: truss_opts | None = None):
                                    ctypes.byref(opts) if opts is not None else None),
            "truss_ctx_create")
     return ctx
+
+
+def truss_ctx_set_opts(ctx, opts: truss_opts) -> None:
+    _check(_lib().truss_ctx_set_opts(ctx, ctypes.byref(opts)), "truss_ctx_set_opts")
 
 
 def truss_ctx_destroy(ctx) -> None:
@@ -310,6 +317,17 @@ class Context:
         for k, v in kw.items():
             setattr(o, k, v)
         self.ctx = truss_ctx_create(device, o)
+
+    def set_opts(self, profile: bool = False, count_bytes: bool = False, wait_limit_ns: int = 0,
+                 **kw):
+        """Replace every option of the context (unnamed ones return to 0)."""
+        o = truss_opts()
+        o.profile = int(profile)
+        o.count_bytes = int(count_bytes)
+        o.wait_limit_ns = int(wait_limit_ns)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        truss_ctx_set_opts(self.ctx, o)
 
     def close(self):
         if self.ctx is not None:
