@@ -33,11 +33,14 @@
 // reservation per buffer, and per-level reductions (minimum residual, alive
 // count) are combined per block first: a single global counter hit by every
 // warp would serialise the whole grid on one L2 address.
-// The queues use monotonically increasing 64-bit counters (never reset).  The
-// block that completes a grid barrier copies them into a snapshot slot of
-// that barrier's generation before releasing it, and every block takes its
-// next bases from the snapshot: a block that leaves the barrier early may
-// already append to the live counters while a slow one has not read them.
+// Every scan and every sub-round is one phase, ended by one grid barrier.
+// Appends of phase p reserve space through counter slot p % 3 (frontier
+// items qf, alive-list entries qa), which is read after the barrier that
+// ends p.  The leader zeroes slot (p+1) % 3 during phase p: that slot was
+// last read at the start of phase p-1, and every block has passed the
+// barrier ending p-1 before the leader can be in phase p.  A block that
+// leaves a barrier early therefore never appends to a counter that a slow
+// block has still to read.
 //
 // Edge state is one int per edge, stamp[e]: 0 = alive, s = in the frontier of
 // sub-round s, 0 < stamp < s = removed earlier.  A partner pushed during
@@ -66,15 +69,13 @@ constexpr int kWQ = 64;    // work items staged per warp
 constexpr int kWA = 128;   // alive-list entries staged per warp
 
 struct PeelCtl {
-  unsigned bar_count;
-  unsigned bar_gen;
+  unsigned long long bar;    // barrier arrivals so far (never reset)
   int err;
   int pad0;
-  unsigned long long qf;  // frontier items appended so far (F and N alternate)
-  unsigned long long qa;  // alive-list entries appended so far
-  int minres[3];          // per scan (slot = scan index % 3)
-  int live[3];            // alive edges left after each scan
-  unsigned long long snap[2][2];  // qf, qa at the last two barriers
+  unsigned long long qf[3];  // frontier items appended in phase p (slot p % 3)
+  unsigned long long qa[3];  // alive-list entries appended in phase p
+  int minres[3];             // per scan (slot = scan index % 3)
+  int live[3];               // alive edges left after each scan
   int levels, subrounds, kmax, ntrace;
   unsigned long long entries, decrements, scanned;
 };
@@ -96,31 +97,27 @@ struct PeelArgs {
   long long wait_ns;
 };
 
-// Grid-wide barrier with a time limit.  On return every thread of the block
-// sees in `snap` the values of qf and qa at the moment the last block
-// arrived.  Returns false if any block has recorded an error (including this
-// barrier timing out).
-__device__ bool grid_barrier(PeelCtl *c, long long wait_ns, unsigned long long *snap) {
+// Grid-wide barrier with a time limit.  Arrival is one atomic increment of a
+// counter that is never reset: the block whose increment returned `old`
+// waits until the counter reaches the next multiple of the grid size (every
+// block arrives exactly once per barrier, so the arrivals of one barrier are
+// a run of gridDim.x consecutive values).  Returns false if any block has
+// recorded an error (including this barrier timing out).
+__device__ bool grid_barrier(PeelCtl *c, long long wait_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *vgen = &c->bar_gen;
-    const unsigned g = *vgen;
     __threadfence();
-    const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      __threadfence();
-      volatile unsigned long long *sn = c->snap[g & 1];
-      sn[0] = __ldcg(&c->qf);
-      sn[1] = __ldcg(&c->qa);
-      atomicExch(&c->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&c->bar_gen, 1u);
-    } else {
+    const unsigned long long old = atomicAdd(&c->bar, 1ull);
+    const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
+    if (old + 1 != target) {
+      volatile unsigned long long *vb = &c->bar;
+      volatile int *verr = &c->err;
       const unsigned long long t0 = global_ns();
       int spins = 0;
-      while (*vgen == g) {
-        if (++spins > 64) __nanosleep(64);
+      while (*vb < target) {
+        if (++spins > 32) __nanosleep(32);
+        if (*verr != 0) break;
         if ((long long)(global_ns() - t0) > wait_ns) {
           atomicExch(&c->err, TRUSS_ETIMEOUT);
           break;
@@ -128,9 +125,6 @@ __device__ bool grid_barrier(PeelCtl *c, long long wait_ns, unsigned long long *
       }
     }
     __threadfence();
-    volatile unsigned long long *sn = c->snap[g & 1];
-    snap[0] = sn[0];
-    snap[1] = sn[1];
     s_ok = (*(volatile int *)&c->err) == 0;
   }
   __syncthreads();
@@ -149,12 +143,12 @@ struct WarpBuf {
 
 // Write the staged items to queue Q with one reservation.
 __device__ __forceinline__ void flush_items(const PeelArgs &a, WarpBuf &wb, int4 *Q,
-                                            unsigned long long base_q) {
+                                            unsigned long long *qctr) {
   if (wb.ni == 0) return;
   const int lane = lane_id();
   unsigned long long b = 0;
-  if (lane == 0) b = atomicAdd(&a.ctl->qf, (unsigned long long)wb.ni);
-  const long long b0 = (long long)(__shfl_sync(TR_FULL, b, 0) - base_q);
+  if (lane == 0) b = atomicAdd(qctr, (unsigned long long)wb.ni);
+  const long long b0 = (long long)__shfl_sync(TR_FULL, b, 0);
   for (int t = lane; t < wb.ni; t += 32)
     if (b0 + t < a.item_cap) Q[b0 + t] = wb.items[t];
   __syncwarp();
@@ -162,12 +156,12 @@ __device__ __forceinline__ void flush_items(const PeelArgs &a, WarpBuf &wb, int4
 }
 
 __device__ __forceinline__ void flush_alive(const PeelArgs &a, WarpBuf &wb, int32_t *A2,
-                                            unsigned long long base_a) {
+                                            unsigned long long *actr) {
   if (wb.na == 0) return;
   const int lane = lane_id();
   unsigned long long b = 0;
-  if (lane == 0) b = atomicAdd(&a.ctl->qa, (unsigned long long)wb.na);
-  const long long b0 = (long long)(__shfl_sync(TR_FULL, b, 0) - base_a);
+  if (lane == 0) b = atomicAdd(actr, (unsigned long long)wb.na);
+  const long long b0 = (long long)__shfl_sync(TR_FULL, b, 0);
   for (int t = lane; t < wb.na; t += 32)
     if (b0 + t < a.m) A2[b0 + t] = wb.alive[t];
   __syncwarp();
@@ -176,11 +170,11 @@ __device__ __forceinline__ void flush_alive(const PeelArgs &a, WarpBuf &wb, int3
 
 // Queue the alive edges of the lanes with `keep` for the rewritten list.
 __device__ __forceinline__ void push_alive(const PeelArgs &a, bool keep, int e, WarpBuf &wb,
-                                           int32_t *A2, unsigned long long base_a) {
+                                           int32_t *A2, unsigned long long *actr) {
   const unsigned mask = __ballot_sync(TR_FULL, keep);
   if (mask == 0) return;
   const int tot = __popc(mask);
-  if (wb.na + tot > kWA) flush_alive(a, wb, A2, base_a);
+  if (wb.na + tot > kWA) flush_alive(a, wb, A2, actr);
   if (keep) wb.alive[wb.na + __popc(mask & ((1u << lane_id()) - 1u))] = e;
   __syncwarp();
   wb.na += tot;
@@ -191,7 +185,7 @@ __device__ __forceinline__ void push_alive(const PeelArgs &a, bool keep, int e, 
 // the warp's staging buffer; a batch larger than the buffer is written
 // straight to Q with its own reservation.
 __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, WarpBuf &wb,
-                                           int4 *Q, unsigned long long base_q, int stamp_val) {
+                                           int4 *Q, unsigned long long *qctr, int stamp_val) {
   const int lane = lane_id();
   int n = 0, L = 0;
   int64_t lb = 0;
@@ -208,11 +202,11 @@ __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, 
   long long b0;
   if (tot > kWQ) {
     unsigned long long b = 0;
-    if (lane == 31) b = atomicAdd(&a.ctl->qf, (unsigned long long)tot);
-    b0 = (long long)(__shfl_sync(TR_FULL, b, 31) - base_q);
+    if (lane == 31) b = atomicAdd(qctr, (unsigned long long)tot);
+    b0 = (long long)__shfl_sync(TR_FULL, b, 31);
     dst = Q;
   } else {
-    if (wb.ni + tot > kWQ) flush_items(a, wb, Q, base_q);
+    if (wb.ni + tot > kWQ) flush_items(a, wb, Q, qctr);
     b0 = wb.ni;
     dst = wb.items;
   }
@@ -273,7 +267,7 @@ __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int
 template <int NE>
 __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bool *v,
                                        const int2 *p, int k, int s, WarpBuf &wb, int4 *N,
-                                       unsigned long long base_f, unsigned long long &n_dec) {
+                                       unsigned long long *qctr, unsigned long long &n_dec) {
   bool d1[NE], d2[NE];
 #pragma unroll
   for (int i = 0; i < NE; i++) decide(a, v[i], e[i], p[i], s, d1[i], d2[i]);
@@ -290,8 +284,8 @@ __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bo
   if (__any_sync(TR_FULL, any)) {
 #pragma unroll
     for (int i = 0; i < NE; i++) {
-      push_items(a, o1[i] == k - 1, p[i].x, wb, N, base_f, s + 1);
-      push_items(a, o2[i] == k - 1, p[i].y, wb, N, base_f, s + 1);
+      push_items(a, o1[i] == k - 1, p[i].x, wb, N, qctr, s + 1);
+      push_items(a, o2[i] == k - 1, p[i].y, wb, N, qctr, s + 1);
     }
   }
 }
@@ -307,7 +301,6 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   const int64_t twarps = (int64_t)gridDim.x * kWarps;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   PeelCtl *ctl = a.ctl;
-  __shared__ unsigned long long snap[2];  // qf, qa at the last barrier
   __shared__ int4 s_items[kWarps][kWQ];
   __shared__ int32_t s_alive[kWarps][kWA];
   __shared__ int s_minres, s_live;
@@ -319,7 +312,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   __syncthreads();
 
   int k = 2, s = 1, sc = 0;
-  unsigned long long base_f = 0, base_a = 0;
+  unsigned ph = 0;  // phase index (scans and sub-rounds)
   int32_t *alive = a.alive0, *alive2 = a.alive1;
   int4 *F = a.Q0, *N = a.Q1;
   int64_t nAlive = a.m;
@@ -333,9 +326,12 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
       a.trace[ctl->ntrace++] = make_int4(k, -1, (int)(uint32_t)t, (int)(uint32_t)(t >> 32));
     }
     const int slot = sc % 3;
+    unsigned long long *qf = &ctl->qf[ph % 3], *qa = &ctl->qa[ph % 3];
     if (leader) {
       ctl->minres[(sc + 1) % 3] = INT_MAX;
       ctl->live[(sc + 1) % 3] = 0;
+      ctl->qf[(ph + 1) % 3] = 0;
+      ctl->qa[(ph + 1) % 3] = 0;
     }
     int wmin = INT_MAX, wlive = 0;
     // 4 x 32 entries per warp iteration: all loads are issued before any
@@ -358,15 +354,15 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         const bool live = e[u] >= 0 && st[u] == 0;
         const bool toF = live && r[u] <= k - 2;
         const bool keep = live && !toF;
-        push_items(a, toF, e[u], wb, F, base_f, s);
-        if (compact) push_alive(a, keep, e[u], wb, alive2, base_a);
+        push_items(a, toF, e[u], wb, F, qf, s);
+        if (compact) push_alive(a, keep, e[u], wb, alive2, qa);
         wmin = min(wmin, __reduce_min_sync(TR_FULL, keep ? r[u] : INT_MAX));
         wlive += __popc(__ballot_sync(TR_FULL, keep));
         n_scan += (e[u] >= 0);
       }
     }
-    flush_items(a, wb, F, base_f);
-    if (compact) flush_alive(a, wb, alive2, base_a);
+    flush_items(a, wb, F, qf);
+    if (compact) flush_alive(a, wb, alive2, qa);
     if (lane == 0) {
       if (wmin != INT_MAX) atomicMin(&s_minres, wmin);
       if (wlive) atomicAdd(&s_live, wlive);
@@ -378,14 +374,13 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
       s_minres = INT_MAX;
       s_live = 0;
     }
-    if (!grid_barrier(ctl, a.wait_ns, snap)) return;
+    if (!grid_barrier(ctl, a.wait_ns)) return;
+    ph++;
     const int minres = __ldcg(&ctl->minres[slot]);
     const int64_t live = __ldcg(&ctl->live[slot]);
-    const int64_t nF = (int64_t)(snap[0] - base_f);
-    base_f = snap[0];
+    const int64_t nF = (int64_t)__ldcg(qf);
     if (compact) {
-      nAlive = (int64_t)(snap[1] - base_a);
-      base_a = snap[1];
+      nAlive = (int64_t)__ldcg(qa);
       int32_t *t = alive;
       alive = alive2;
       alive2 = t;
@@ -404,6 +399,11 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         const unsigned long long t = global_ns();
         a.trace[ctl->ntrace++] = make_int4(k, (int)min(nCur, (int64_t)INT_MAX),
                                            (int)(uint32_t)t, (int)(uint32_t)(t >> 32));
+      }
+      unsigned long long *qn = &ctl->qf[ph % 3];
+      if (leader) {
+        ctl->qf[(ph + 1) % 3] = 0;
+        ctl->qa[(ph + 1) % 3] = 0;
       }
       const int grp = lane >> 3, j = lane & 7;
       for (int64_t base = gwarp * 4 * G; base < nCur; base += twarps * 4 * G) {
@@ -443,12 +443,12 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           vv[2 * g + 1] = vv[2 * g + 1] && r[g] > 0;
           n_entries += (unsigned long long)(vv[2 * g] + vv[2 * g + 1]);
         }
-        charge<2 * G>(a, ee, vv, pp, k, s, wb, N, base_f, n_dec);
+        charge<2 * G>(a, ee, vv, pp, k, s, wb, N, qn, n_dec);
       }
-      flush_items(a, wb, N, base_f);
-      if (!grid_barrier(ctl, a.wait_ns, snap)) return;
-      const int64_t nN = (int64_t)(snap[0] - base_f);
-      base_f = snap[0];
+      flush_items(a, wb, N, qn);
+      if (!grid_barrier(ctl, a.wait_ns)) return;
+      ph++;
+      const int64_t nN = (int64_t)__ldcg(qn);
       s++;
       if (leader) ctl->subrounds++;
       if (nN == 0) break;

@@ -309,6 +309,20 @@ __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
 // Dense triangle lists from the per-edge records: e's own records go first
 // (list slots known), the two partners take a slot from their cursors
 // (starting after their own records).
+// Dense triangle lists from the records, in two passes so that the scattered
+// 8-byte list writes of each pass land in a small window of `pairs` that L2
+// can merge into whole sectors before they reach DRAM.  The list of edge x
+// is pairs[toff[x] .. toff[x] + sup[x]); its first cuv[x] entries are the
+// triangles x closes as the walked edge, in record order, and cur[x] hands
+// out the rest.
+//
+// Pass 1 (k_lists_from_records, edges in id order = grouped by owner u): for
+// each record (e_uw, e_vw) of walked edge e_uv it writes e_uv's own entry
+// (contiguous) and e_uw's entry; e_uw lies in out(u), whose lists are one
+// contiguous stretch of `pairs`.
+// Pass 2 (k_lists_vw, walked edges grouped by their head v): e_vw's entry;
+// e_vw lies in out(v), so a warp working on v's in-edges writes into v's
+// stretch.
 __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2 *tb,
                                      const int32_t *cuv, const int64_t *toff,
                                      unsigned long long *cur, int2 *pairs, int64_t entries,
@@ -333,17 +347,52 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
         const int2 rec = __ldg(&tb[orr + j]);  // (e_uw, e_vw) of triangle on e_uv = eo
         const int64_t x1 = ol + j;
         const int64_t x2 = (int64_t)atomicAdd(&cur[rec.x], 1ull);
-        const int64_t x3 = (int64_t)atomicAdd(&cur[rec.y], 1ull);
-        if (x1 < entries && x2 < entries && x3 < entries) {
+        if (x1 < entries && x2 < entries) {
           pairs[x1] = rec;
           pairs[x2] = make_int2(eo, rec.y);
-          pairs[x3] = make_int2(eo, rec.x);
         } else {
           atomicExch(err, TRUSS_ECHECK);
         }
       }
     }
   }
+}
+
+// inedge[0 .. m) = the oriented edges sorted by head v (pass 2's order).
+__global__ void k_lists_vw(int64_t m, const int32_t *inedge, const int64_t *tbpre,
+                           const int2 *tb, const int32_t *cuv, unsigned long long *cur,
+                           int2 *pairs, int64_t entries, int *err) {
+  const int lane = lane_id();
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gw * 32; base < m; base += nw * 32) {
+    const int64_t i = base + lane;
+    const int e = i < m ? __ldg(&inedge[i]) : 0;
+    const int c = i < m ? __ldg(&cuv[e]) : 0;
+    const int64_t r0 = i < m ? __ldg(&tbpre[e]) : 0;
+    const int P = warp_incl_scan(c);
+    const int total = __shfl_sync(TR_FULL, P, 31);
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      const int o = warp_owner(P, t < total ? t : total - 1);
+      const int64_t orr = __shfl_sync(TR_FULL, r0, o);
+      const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
+      const int eo = __shfl_sync(TR_FULL, e, o);
+      if (t < total) {
+        const int j = t - (oP - oc);
+        const int2 rec = __ldg(&tb[orr + j]);
+        const int64_t x3 = (int64_t)atomicAdd(&cur[rec.y], 1ull);
+        if (x3 < entries) pairs[x3] = make_int2(eo, rec.x);
+        else atomicExch(err, TRUSS_ECHECK);
+      }
+    }
+  }
+}
+
+__global__ void k_edge_ids(int64_t m, int32_t *ids) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    ids[e] = (int32_t)e;
 }
 
 // Cursors for k_lists_from_records: after each edge's own records.
@@ -439,9 +488,10 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
       TR_CUDA(cudaMemcpyAsync(&R, tbpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TR_CUDA(cudaStreamSynchronize(s));
   }
-  // Records need 8 R bytes now and the lists later at most 24 R more; use
-  // them only when that fits in free device memory (else the list pass walks
-  // the graph a second time).
+  // Records need 8 R bytes now and the lists later at most 24 R more, plus
+  // 16 m for the head-ordered edge index of the second list pass; use them
+  // only when that fits in free device memory (else the list pass walks the
+  // graph a second time).
   int2 *recs = nullptr;
   int32_t *cuv = nullptr;
   if (cfg.records && R > 0) {
@@ -450,7 +500,7 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
       cudaGetLastError();
       fr = 0;
     }
-    const double need = 32.0 * (double)R + 4.0 * (double)m;
+    const double need = 32.0 * (double)R + 20.0 * (double)m;
     if (need * 1.05 < (double)fr + (double)A.unused()) {
       recs = A.get<int2>(R);
       cuv = A.get<int32_t>(m);
@@ -511,11 +561,27 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
     TR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     k_cursors_rec<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.cuv, cur);
     TR_LAUNCHED();
+    // head-ordered index of the oriented edges for pass 2
+    uint32_t *hk = A.get<uint32_t>(m);
+    int32_t *ids = A.get<int32_t>(m), *inedge = A.get<int32_t>(m);
+    if (!hk || !ids || !inedge) return TRUSS_ENOMEM;
+    k_edge_ids<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, ids);
+    TR_LAUNCHED();
+    const int vb = bits_for(g.n > 1 ? (uint64_t)(g.n - 1) : 1);
+    size_t tbytes = 0;
+    TR_TRY(sort_pairs_u32(nullptr, &tbytes, (const uint32_t *)g.adjp, hk, ids, inedge, m, 0, vb,
+                          s));
+    void *tmp = A.alloc(tbytes);
+    if (!tmp) return TRUSS_ENOMEM;
+    TR_TRY(sort_pairs_u32(tmp, &tbytes, (const uint32_t *)g.adjp, hk, ids, inedge, m, 0, vb, s));
     int dev = 0, sms = cfg.sms;
     TR_CUDA(cudaGetDevice(&dev));
     if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     k_lists_from_records<<<sms * 8, 256, 0, s>>>(m, so.tbpre, so.tb, so.cuv, so.toff, cur, pairs,
                                                  so.entries, err);
+    TR_LAUNCHED();
+    k_lists_vw<<<sms * 8, 256, 0, s>>>(m, inedge, so.tbpre, so.tb, so.cuv, cur, pairs,
+                                       so.entries, err);
     TR_LAUNCHED();
     int h_err = 0;
     TR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -593,10 +659,13 @@ int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records,
   TR_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
   TR_CUDA(cudaStreamSynchronize(s));
   // per triangle: the (v, w) count RMW, plus the 8-B record when recording;
-  // lists from records: record read, three entries, two cursor RMWs (48 B);
-  // lists by a second walk: the walk again plus 60 B per triangle
+  // lists from records: the record read by both passes, three entries, two
+  // cursor RMWs (56 B), and per edge the cursor set-up and both passes'
+  // offset/count reads (56 B; the head-order sort is not counted); lists by
+  // a second walk: the walk again plus 60 B per triangle
   *b_sup = (double)h + (records ? 16.0 : 8.0) * (double)triangles;
-  *b_lists = records ? 48.0 * (double)triangles : (double)h + 60.0 * (double)triangles;
+  *b_lists = records ? 56.0 * (double)triangles + 56.0 * (double)g.m
+                     : (double)h + 60.0 * (double)triangles;
   return TRUSS_OK;
 }
 
