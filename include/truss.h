@@ -85,8 +85,9 @@ typedef struct truss_opts {
   /* Target walk cost (out-list entries) of one warp range of the support
    * walk (0 = 16384). */
   int32_t support_range_work;
-  /* Fixed cost, in out-list entries, added per walked edge when the support
-   * walk is split into equal-cost ranges (0 = none). */
+  /* Fixed cost, in out-list entries, charged for every oriented edge when
+   * the support walk is split into equal-cost ranges (0 = 64, negative =
+   * none). */
   int32_t support_pair_cost;
   int32_t reserved[7];
 } truss_opts;

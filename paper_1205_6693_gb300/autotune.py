@@ -34,7 +34,7 @@ from typing import Callable
 SPACE: dict[str, tuple[int, ...]] = {
     "support_range_work": (0, 4096, 8192, 32768, 65536),
     "support_stage_max": (0, 64, 128, 256),
-    "support_pair_cost": (0, 4, 16, 64),
+    "support_pair_cost": (0, 16, 32, 128, 256),
     "peel_variant": (0, 1, 3),
 }
 # Stage-time keys of truss_last_stats each knob is judged on.

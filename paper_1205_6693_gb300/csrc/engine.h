@@ -101,7 +101,7 @@ struct SupportCfg {
   int block = 256;
   int sms = 0;
   bool records = false;  // also record triangles for the list pass (if memory allows)
-  int pair_cost = 0;      // fixed cost of walking one edge, in out-list entries
+  int pair_cost = 0;      // fixed cost per oriented edge, in out-list entries (0 = default, <0 = none)
   int64_t range_work = 0; // walk cost per range (0 = default)
   int stage_max = 0;      // stage out-lists of at most this many entries (0 = capacity)
 };

@@ -40,18 +40,24 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int64_t kRangeWork = 16384;  // target walk cost per range
+constexpr int kEdgeCost = 64;          // fixed walk cost per oriented edge (entries)
 // Out-list entries staged per warp: counting pass (int32 counters) and list
 // pass (int64 cursors).
 template <int MODE>
 struct Cap {
   static constexpr int value = MODE == 0 ? 512 : 256;
 };
-constexpr int kAChunk = 512;  // out(v) entries staged per warp per chunk
+constexpr int kAChunk = 512;     // out(v) entries staged per warp per chunk (merge path)
+constexpr int kHashSlots = 2048; // per-warp position table of a staged out(u) (MODE 0)
 template <int MODE>
 __host__ __device__ constexpr size_t warp_smem() {
-  // counters (int32) or cursors (int64), L (int32), out(v) chunk (int32)
-  return (size_t)Cap<MODE>::value * ((MODE == 0 ? 4 : 8) + 4) + (size_t)kAChunk * 4;
+  // counters (int32) or cursors (int64), L (int32), then MODE 0: the
+  // position table (uint16), which the merge path of unstaged owners reuses
+  // as its out(v) chunk; MODE 1: the out(v) chunk (int32)
+  return (size_t)Cap<MODE>::value * ((MODE == 0 ? 4 : 8) + 4) +
+         (MODE == 0 ? (size_t)kHashSlots * 2 : (size_t)kAChunk * 4);
 }
+static_assert(kHashSlots * 2 >= kAChunk * 4, "chunk buffer aliases the position table");
 
 struct SupArgs {
   int64_t n, m;
@@ -221,9 +227,100 @@ __device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList
   }
 }
 
+// Slot of vertex w in a position table of 2^(32 - sh) slots.
+__device__ __forceinline__ unsigned hslot(int w, int sh) {
+  return ((unsigned)w * 0x9E3779B1u) >> sh;
+}
+
+// MODE 0 with out(u) staged (Ls, d entries): the triangles of the edges
+// (u, Ls[i]) for i in [i0, i1).  out(u) goes into a hash table Hs of
+// positions + 1 (linear probing, load factor <= 1/4); each entry w of out(v)
+// is looked up there, and a hit at position q is the triangle (u, v, w) with
+// e_uv = bu + i, e_uw = bu + q and e_vw = w's position in adjp.  Every such
+// w ranks above v, so nothing outside out(u) after v can match.  A triangle
+// adds 1 to supB[e_vw] and to Cs[q] (e_uw's owner count), and the pair's
+// total goes to Cs[i]; with records on, the triangle is written as
+// (e_uw, e_vw) to e_uv's record region, its index inside the region taken
+// from a warp ballot.
+__device__ __forceinline__ void probe_walk(const SupArgs &a, int64_t bu, const int32_t *Ls,
+                                           int d, int32_t *Cs, unsigned short *Hs, int i0,
+                                           int i1) {
+  const int lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  int lg = 32 - __clz(max(8 * d - 1, 63));  // ceil(log2(8 d)), at least 6
+  lg = min(lg, 11);
+  const int S = 1 << lg, sh = 32 - lg;
+  for (int t = lane; t < S / 2; t += 32) ((uint32_t *)Hs)[t] = 0u;
+  __syncwarp();
+  for (int q = lane; q < d; q += 32) {
+    unsigned sl = hslot(Ls[q], sh);
+    while (atomicCAS(&Hs[sl], (unsigned short)0, (unsigned short)(q + 1)) != 0)
+      sl = (sl + 1) & (unsigned)(S - 1);
+  }
+  __syncwarp();
+  const int Lmax = Ls[d - 1];
+  for (int c0 = i0; c0 < i1; c0 += 32) {
+    // offsets (and record bases) of 32 pairs at once
+    const int i = c0 + lane;
+    const bool valid = i < i1;
+    const int v = valid ? Ls[i] : 0;
+    const int64_t vb = valid ? __ldg(&a.offp[v]) : 0;
+    const int len = valid ? (int)(__ldg(&a.offp[v + 1]) - vb) : 0;
+    const int64_t rb = (valid && a.tb) ? __ldg(&a.tbpre[bu + i]) : 0;
+    const int nv = min(32, i1 - c0);
+    for (int o = 0; o < nv; o++) {
+      const int64_t ob = __shfl_sync(TR_FULL, vb, o);
+      const int olen = __shfl_sync(TR_FULL, len, o);
+      const int64_t tbase = __shfl_sync(TR_FULL, rb, o);
+      const int io = c0 + o;
+      int cnt = 0;  // triangles of this pair so far (warp-uniform)
+      for (int t0 = 0; t0 < olen; t0 += 128) {
+        int w[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int t = t0 + k * 32 + lane;
+          w[k] = t < olen ? __ldg(&a.adjp[ob + t]) : INT_MAX;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          int q = -1;
+          if (w[k] <= Lmax) {
+            unsigned sl = hslot(w[k], sh);
+            for (;;) {
+              const int p = Hs[sl];
+              if (p == 0) break;
+              if (Ls[p - 1] == w[k]) {
+                q = p - 1;
+                break;
+              }
+              sl = (sl + 1) & (unsigned)(S - 1);
+            }
+          }
+          const unsigned hm = __ballot_sync(TR_FULL, q >= 0);
+          if (q >= 0) {
+            const int64_t evw = ob + t0 + k * 32 + lane;
+            atomicAdd(&a.supB[evw], 1);
+            atomicAdd(&Cs[q], 1);
+            if (a.tb)
+              a.tb[tbase + cnt + __popc(hm & lt)] = make_int2((int)(bu + q), (int)evw);
+          }
+          cnt += __popc(hm);
+        }
+        // out(v) is sorted: once an entry exceeds max out(u), none later can match
+        if (__shfl_sync(TR_FULL, w[3], 31) > Lmax) break;
+      }
+      if (lane == 0) {
+        if (a.tb) a.cuv[bu + io] = cnt;
+        if (cnt) atomicAdd(&Cs[io], cnt);
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // Warps take equal-cost ranges of oriented edges round-robin.
 template <int MODE>
-__global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
+__global__ void __launch_bounds__(kBlock, MODE == 0 ? 3 : 4) k_support(SupArgs a) {
   constexpr int CAP = Cap<MODE>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -231,7 +328,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
   // layout: counters/cursors (8-byte aligned first), then L, then the out(v) chunk
   void *Cs = base;
   int32_t *Ls = (int32_t *)(base + (size_t)CAP * (MODE == 0 ? 4 : 8));
-  int32_t *Abuf = Ls + CAP;
+  unsigned short *Hs = (unsigned short *)(Ls + CAP);  // MODE 0 staged owners
+  int32_t *Abuf = Ls + CAP;                           // merge path
   __shared__ int s_uvc[kBlock / 32];
   int *uvc = &s_uvc[warp];
   if (lane == 0) *uvc = 0;
@@ -263,8 +361,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
         __syncwarp();
         C = Cs;
         if (MODE == 1 && !whole) C = a.curA + bu;  // cursors shared by several ranges
-        OutList<true> ol{Ls, d};
-        walk<MODE, true>(a, bu, ol, C, i0, i1, Abuf, uvc);
+        if (MODE == 0) {
+          probe_walk(a, bu, Ls, d, (int32_t *)Cs, Hs, i0, i1);
+        } else {
+          OutList<true> ol{Ls, d};
+          walk<MODE, true>(a, bu, ol, C, i0, i1, Abuf, uvc);
+        }
       } else {
         C = MODE == 0 ? (void *)(a.supA + bu) : (void *)(a.curA + bu);
         OutList<false> ol{a.adjp + bu, d};
@@ -284,21 +386,27 @@ __global__ void __launch_bounds__(kBlock, 4) k_support(SupArgs a) {
 }
 
 // Walk cost of each oriented edge: |out(v)| for (u, v) unless v is the last
-// entry of out(u); and the most triangles (u, v, w) it can close,
-// min(|out(v)|, entries of out(u) after v).
+// entry of out(u), plus `edge_cost` for every edge; and the most triangles
+// (u, v, w) it can close, min(|out(v)|, entries of out(u) after v).  The
+// fixed part stands for what a warp pays per edge whatever the lists: the
+// offsets it loads and, for owners with a single out-edge (the long run of
+// degree-1 vertices at the bottom of the degree order), the step to the
+// next owner.  Without it that run is free and falls into one range, which
+// one warp then steps through owner by owner.
 __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
-                            const int32_t *esrc, int64_t *cost, int64_t *bound, int pair_cost) {
+                            const int32_t *esrc, int64_t *cost, int64_t *bound, int edge_cost) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t c = 0, b = 0;
     if (e < m) {
       const int u = esrc[e];
       const int64_t end = offp[u + 1];
+      c = edge_cost;
       if (e != end - 1) {
         const int v = adjp[e];
         const int64_t a = offp[v + 1] - offp[v];
         b = min(a, end - 1 - e);
-        c = a + pair_cost;
+        c += a;
       }
     }
     cost[e] = c;
@@ -475,7 +583,7 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
   int64_t W = 0, R = 0;
   if (m > 0) {
     k_walk_cost<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, g.offp, g.adjp, g.esrc, wcost,
-                                                                wbound, cfg.pair_cost);
+                                                                wbound, cfg.pair_cost > 0 ? cfg.pair_cost : cfg.pair_cost < 0 ? 0 : kEdgeCost);
     TR_LAUNCHED();
     size_t tb = 0;
     TR_TRY(exclusive_sum_i64(nullptr, &tb, wcost, wpre, m + 1, s));
