@@ -385,6 +385,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rmat-scale", type=int, default=20,
+                    help="single mode: R-MAT scale of the graph (20 = the mid workload; "
+                         "smaller scales are profiling cases)")
     ap.add_argument("--no-tune", action="store_true",
                     help="use cached or default schedules; never run the autotuner")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
@@ -410,7 +413,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    n, src_np, dst_np = graphgen.mid()
+    if args.rmat_scale == 20:
+        n, src_np, dst_np = graphgen.mid()
+        workload = WORKLOAD
+    else:
+        sc = args.rmat_scale
+        src_np, dst_np = graphgen.rmat_raw(sc, 16 * 2 ** sc, seed=1)
+        n = 2 ** sc
+        workload = (f"R-MAT scale {sc}, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
+                    f"seed 1 (profiling case)")
     rows = len(src_np)
     src = torch.from_numpy(src_np).to(dev)
     dst = torch.from_numpy(dst_np).to(dev)
@@ -500,10 +511,10 @@ def main():
     kernel_name = {"support": "k_support<0>",
                    "lists": "k_lists_from_records",
                    "peel": "k_peel (persistent, cooperative)"}[dom]
-    traffic = traffic_for(dom)
+    traffic = traffic_for(dom) if args.rmat_scale == 20 else None
 
     cpu = None
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and args.rmat_scale == 20:
         m_s, dt = oracle_rate(CPU_SAMPLE_ROWS)
         cpu = {"value": m_s / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": (f"first {CPU_SAMPLE_ROWS:,} rows of the workload ({m_s:,} distinct "
@@ -513,7 +524,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": m, "rows": rows, "triangles": st["triangles"],
+        "config": {"workload": workload, "m": m, "rows": rows, "triangles": st["triangles"],
                    "kmax": kmax, "parallelism": f"replicas x{ws}", "l2_flush": True,
                    "stage_ms_median": {k: round(v, 3) for k, v in med.items()},
                    "levels": st["levels"], "subrounds": st["subrounds"],

@@ -431,6 +431,11 @@ __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
 // Pass 2 (k_lists_vw, walked edges grouped by their head v): e_vw's entry;
 // e_vw lies in out(v), so a warp working on v's in-edges writes into v's
 // stretch.
+// A warp takes 32 consecutive entries of an edge order at a time and walks
+// their records 4 per lane per step, so that 4 record loads and then 4
+// cursor atomics are in flight per lane before any store needs their results.
+constexpr int kListU = 4;
+
 __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2 *tb,
                                      const int32_t *cuv, const int64_t *toff,
                                      unsigned long long *cur, int2 *pairs, int64_t entries,
@@ -444,20 +449,30 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
     const int64_t r0 = e < m ? tbpre[e] : 0, l0 = e < m ? toff[e] : 0;
     const int P = warp_incl_scan(c);
     const int total = __shfl_sync(TR_FULL, P, 31);
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      const int o = warp_owner(P, t < total ? t : total - 1);
-      const int64_t orr = __shfl_sync(TR_FULL, r0, o), ol = __shfl_sync(TR_FULL, l0, o);
-      const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
-      if (t < total) {
+    for (int t0 = 0; t0 < total; t0 += 32 * kListU) {
+      int2 rec[kListU];
+      int64_t x1[kListU], x2[kListU];
+      int eo[kListU];
+#pragma unroll
+      for (int k = 0; k < kListU; k++) {
+        const int t = t0 + k * 32 + lane;
+        const int o = warp_owner(P, t < total ? t : total - 1);
+        const int64_t orr = __shfl_sync(TR_FULL, r0, o), ol = __shfl_sync(TR_FULL, l0, o);
+        const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
         const int j = t - (oP - oc);
-        const int eo = (int)(base + o);
-        const int2 rec = __ldg(&tb[orr + j]);  // (e_uw, e_vw) of triangle on e_uv = eo
-        const int64_t x1 = ol + j;
-        const int64_t x2 = (int64_t)atomicAdd(&cur[rec.x], 1ull);
-        if (x1 < entries && x2 < entries) {
-          pairs[x1] = rec;
-          pairs[x2] = make_int2(eo, rec.y);
+        eo[k] = (int)(base + o);
+        x1[k] = ol + j;
+        rec[k] = t < total ? __ldg(&tb[orr + j]) : make_int2(-1, -1);  // (e_uw, e_vw) on e_uv
+      }
+#pragma unroll
+      for (int k = 0; k < kListU; k++)
+        x2[k] = rec[k].x >= 0 ? (int64_t)atomicAdd(&cur[rec[k].x], 1ull) : 0;
+#pragma unroll
+      for (int k = 0; k < kListU; k++) {
+        if (rec[k].x < 0) continue;
+        if (x1[k] < entries && x2[k] < entries) {
+          pairs[x1[k]] = rec[k];
+          pairs[x2[k]] = make_int2(eo[k], rec[k].y);
         } else {
           atomicExch(err, TRUSS_ECHECK);
         }
@@ -480,17 +495,27 @@ __global__ void k_lists_vw(int64_t m, const int32_t *inedge, const int64_t *tbpr
     const int64_t r0 = i < m ? __ldg(&tbpre[e]) : 0;
     const int P = warp_incl_scan(c);
     const int total = __shfl_sync(TR_FULL, P, 31);
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      const int o = warp_owner(P, t < total ? t : total - 1);
-      const int64_t orr = __shfl_sync(TR_FULL, r0, o);
-      const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
-      const int eo = __shfl_sync(TR_FULL, e, o);
-      if (t < total) {
+    for (int t0 = 0; t0 < total; t0 += 32 * kListU) {
+      int2 rec[kListU];
+      int64_t x3[kListU];
+      int eo[kListU];
+#pragma unroll
+      for (int k = 0; k < kListU; k++) {
+        const int t = t0 + k * 32 + lane;
+        const int o = warp_owner(P, t < total ? t : total - 1);
+        const int64_t orr = __shfl_sync(TR_FULL, r0, o);
+        const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
+        eo[k] = __shfl_sync(TR_FULL, e, o);
         const int j = t - (oP - oc);
-        const int2 rec = __ldg(&tb[orr + j]);
-        const int64_t x3 = (int64_t)atomicAdd(&cur[rec.y], 1ull);
-        if (x3 < entries) pairs[x3] = make_int2(eo, rec.x);
+        rec[k] = t < total ? __ldg(&tb[orr + j]) : make_int2(-1, -1);
+      }
+#pragma unroll
+      for (int k = 0; k < kListU; k++)
+        x3[k] = rec[k].y >= 0 ? (int64_t)atomicAdd(&cur[rec[k].y], 1ull) : 0;
+#pragma unroll
+      for (int k = 0; k < kListU; k++) {
+        if (rec[k].y < 0) continue;
+        if (x3[k] < entries) pairs[x3[k]] = make_int2(eo[k], rec[k].x);
         else atomicExch(err, TRUSS_ECHECK);
       }
     }
