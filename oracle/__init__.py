@@ -7,7 +7,9 @@ input generator package ``graphgen``.
 
 * ``alg2.c``  -- Algorithm 2 of Wang & Cheng (Section 3.2) in plain C, single
   threaded, with step 2's supports from forward triangle listing.  Wrapped
-  here by :func:`truss`.
+  here by :func:`truss`; :func:`psi` is the upper bound of Procedure 6
+  (Section 6.2) from its definition, and :func:`top` the top-t classes of
+  Algorithm 7 (Section 6.3) read off the full decomposition.
 * ``checks.py`` -- independent checkers written from the definitions: edge
   subset brute force (Definition 2), the literal Algorithm 1 (Section 3.1),
   triple-enumeration support (Definition 1), core numbers, the upper bound
@@ -53,6 +55,8 @@ def _L():
         L.oracle_check_sample.restype = ctypes.c_int64
         L.oracle_check_sample.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p,
                                           _i32p, ctypes.c_int64, _i64p, _i32p]
+        L.oracle_psi.restype = ctypes.c_int
+        L.oracle_psi.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p, _i32p]
         L.oracle_check_valid.restype = ctypes.c_int64
         L.oracle_check_valid.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p,
                                          _i32p]
@@ -92,6 +96,33 @@ def truss(n: int, src, dst, with_truss: bool = True) -> OracleResult:
         raise MemoryError("oracle_truss")
     return OracleResult(sup[:rows], tr[:rows] if with_truss else None, kmax.value, m.value,
                         tri.value)
+
+
+def psi(n: int, src, dst):
+    """Per-row (support, psi) with psi(e) = min{sup(e), x_u, x_v} + 2 of
+    Procedure 6 (Section 6.2), computed from the definition."""
+    src, dst = _c(src), _c(dst)
+    rows = len(src)
+    sup = np.empty(max(rows, 1), np.int32)
+    ps = np.empty(max(rows, 1), np.int32)
+    rc = _L().oracle_psi(n, rows, src.ctypes.data_as(_i32p), dst.ctypes.data_as(_i32p),
+                         sup.ctypes.data_as(_i32p), ps.ctypes.data_as(_i32p))
+    if rc == -1:
+        raise ValueError("vertex id out of range")
+    if rc:
+        raise MemoryError("oracle_psi")
+    return sup[:rows], ps[:rows]
+
+
+def top(n: int, src, dst, t: int):
+    """The top-t k-classes by definition: per-row phi(e) where phi(e) >=
+    k_max - t + 1, else 0 (self-loop rows -1), from the full decomposition
+    (Algorithm 2).  Returns (per-row values, k_max)."""
+    r = truss(n, src, dst)
+    thr = max(r.kmax - t + 1, 2)
+    out = np.where(r.truss >= thr, r.truss, 0).astype(np.int32)
+    out[r.truss < 0] = -1
+    return out, r.kmax
 
 
 def edges(n: int, src, dst):

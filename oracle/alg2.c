@@ -299,6 +299,60 @@ int oracle_truss(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst
   return OR_OK;
 }
 
+/* Largest x such that at least x of the supports of w's incident edges,
+ * leaving out edge `skip`, are >= x (the x_w of Procedure 6, Section 6.2),
+ * by counting: cnt[x] = how many of those supports are >= x, for x <= deg. */
+static int32_t x_excluding(const graph *g, const int32_t *sup, int32_t w, int32_t skip,
+                           int64_t *cnt) {
+  const int64_t d = deg(g, w);
+  for (int64_t x = 0; x <= d; x++) cnt[x] = 0;
+  for (int64_t j = g->off[w]; j < g->off[w + 1]; j++) {
+    int32_t f = g->adje[j];
+    if (f == skip) continue;
+    int64_t s = sup[f] < d ? sup[f] : d;
+    cnt[s]++;
+  }
+  /* suffix sums: cnt[x] = #{supports >= x} (capped supports keep this exact
+   * for every x <= d) */
+  for (int64_t x = d - 1; x >= 0; x--) cnt[x] += cnt[x + 1];
+  int32_t best = 0;
+  for (int64_t x = 0; x <= d; x++)
+    if (cnt[x] >= x) best = (int32_t)x;
+  return best;
+}
+
+/* Per-row psi(e) = min{sup(e), x_u, x_v} + 2 (Procedure 6 with the whole
+ * graph as the neighbourhood subgraph) and sup(e); -1 for self-loop rows. */
+int oracle_psi(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+               int32_t *support_out, int32_t *psi_out) {
+  graph g;
+  int rc = g_build(&g, n, rows, src, dst);
+  if (rc) { g_free(&g); return rc; }
+  int64_t maxd = 0;
+  for (int64_t v = 0; v < n; v++) if (deg(&g, v) > maxd) maxd = deg(&g, v);
+  int32_t *sup = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g.m + 1));
+  int32_t *psi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g.m + 1));
+  int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(maxd + 2));
+  if (!sup || !psi || !cnt) { free(sup); free(psi); free(cnt); g_free(&g); return OR_ENOMEM; }
+  support_forward(&g, sup);
+  for (int64_t e = 0; e < g.m; e++) {
+    int32_t xu = x_excluding(&g, sup, g.eu[e], (int32_t)e, cnt);
+    int32_t xv = x_excluding(&g, sup, g.ev[e], (int32_t)e, cnt);
+    int32_t x = sup[e];
+    if (xu < x) x = xu;
+    if (xv < x) x = xv;
+    psi[e] = x + 2;
+  }
+  for (int64_t r = 0; r < rows; r++) {
+    int32_t e = g.row2e[r];
+    if (support_out) support_out[r] = e < 0 ? -1 : sup[e];
+    if (psi_out) psi_out[r] = e < 0 ? -1 : psi[e];
+  }
+  free(sup); free(psi); free(cnt);
+  g_free(&g);
+  return OR_OK;
+}
+
 /* Edge list in the oracle's canonical order (for tests): eu[e] < ev[e]. */
 int oracle_edges(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
                  int32_t *eu, int32_t *ev, int32_t *row2e, int64_t *m_out) {

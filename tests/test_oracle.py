@@ -78,6 +78,57 @@ def test_fig2_example4_support_and_psi():
     assert all(psi[e] == vals["psi_class5"] for e in edges if classes[e] == 5)
 
 
+def test_fig2_example5_top2():
+    rows = {p[0]: p[1:] for p in _read_fixture("fig2_example5.txt")}
+    classes = fig2()
+    edges = sorted(classes)
+    src = np.array([a for a, _ in edges], np.int32)
+    dst = np.array([b for _, b in edges], np.int32)
+    sup, ps = oracle.psi(12, src, dst)
+    assert int(ps.max()) == int(rows["first_k"][0])
+    t = int(rows["t"][0])
+    top, kmax = oracle.top(12, src, dst, t)
+    key = lambda p: (min(ord(p[0]) - 97, ord(p[1]) - 97), max(ord(p[0]) - 97, ord(p[1]) - 97))
+    want4 = sorted(key(p) for p in rows["class4"])
+    got4 = sorted(e for e, v in zip(edges, top) if v == 4)
+    assert got4 == want4
+    assert sorted(e for e, v in zip(edges, top) if v == 5) == sorted(
+        e for e in edges if classes[e] == 5)
+    assert all(v in (0, 4, 5) for v in top) and kmax == 5
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_psi_counting_equals_definition(seed):
+    """oracle.psi (counting h-index in C) against checks.psi_upper (sorted
+    lists in Python), and Lemma 2 (phi <= psi) with the oracle's phi."""
+    n = 20 + 7 * seed
+    src, dst = graphgen.er(n, 3 * n, seed=seed)
+    perm = graphgen.permutation(n, seed=seed, stream=1)
+    src, dst = graphgen.add_cliques(src, dst, perm[:10], [4, 6])
+    edges = checks.canonical_edges(src, dst)
+    s = np.array([a for a, _ in edges], np.int32)
+    d = np.array([b for _, b in edges], np.int32)
+    sup, ps = oracle.psi(n, s, d)
+    sd = {e: int(x) for e, x in zip(edges, sup)}
+    want = checks.psi_upper(edges, sd)
+    assert [int(x) for x in ps] == [want[e] for e in edges]
+    r = oracle.truss(n, s, d)
+    assert (r.truss <= ps).all()
+
+
+def test_top_t_is_the_full_decomposition_restricted():
+    src, dst = graphgen.rmat_raw(9, 16 << 9, seed=4)
+    r = oracle.truss(1 << 9, src, dst)
+    for t in (1, 2, 5, 1000):
+        top, kmax = oracle.top(1 << 9, src, dst, t)
+        thr = max(kmax - t + 1, 2)
+        keep = r.truss >= thr
+        assert (top[keep] == r.truss[keep]).all()
+        assert (top[(r.truss >= 0) & ~keep] == 0).all()
+        assert (top[r.truss < 0] == -1).all()
+        assert kmax == r.kmax
+
+
 def test_fig2_support_matches_definition():
     edges = sorted(fig2())
     sup, _, r = run(edges)
