@@ -124,6 +124,30 @@ int truss_decompose(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
                     const int32_t *dst, int32_t *support_out, int32_t *truss_out,
                     int32_t *kmax_out, void *cuda_stream);
 
+/* ------------------------------------------------------------- top-t ---- */
+/* Upper bound of the truss number of every edge (Procedure 6, Section 6.2,
+ * with the whole graph as the neighbourhood subgraph):
+ *   psi(e) = min{sup(e), x_u, x_v} + 2, e = (u, v),
+ * where x_w is the largest x such that w has x incident edges other than e
+ * with support >= x.  phi(e) <= psi(e) (Lemma 2).
+ * support_out (nullable): sup(e) per row; psi_out: psi(e) per row; both -1
+ * for self-loop rows.  Errors: TRUSS_EINVAL, TRUSS_ENOMEM, TRUSS_ECUDA. */
+int truss_upper_bound(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                      const int32_t *dst, int32_t *support_out, int32_t *psi_out,
+                      void *cuda_stream);
+
+/* The top-t k-classes, Phi_k for k_max >= k > k_max - t (Algorithm 7,
+ * Section 6.3).  truss_out[r] = phi(e) of row r's edge if phi(e) >= k_max -
+ * t + 1, else 0; -1 for self-loop rows.  kmax_out (nullable, host or device
+ * int32[1]) receives k_max (0 for a graph without edges).  t >= 1; a t of at
+ * least k_max - 1 gives every class.  The library decomposes only the
+ * candidate subgraph of edges whose psi is at least a threshold that it
+ * lowers until it is <= k_max - t + 1 (truss_last_stats: candidates,
+ * rounds).  Errors: TRUSS_EINVAL (also t < 1), TRUSS_ENOMEM, TRUSS_ECUDA,
+ * TRUSS_ETIMEOUT. */
+int truss_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+              int32_t t, int32_t *truss_out, int32_t *kmax_out, void *cuda_stream);
+
 /* ------------------------------------------------------------- batched --- */
 /* Decompose G independent graphs in one pass.  Graph g has n[g] vertices and
  * rows row_off[g] .. row_off[g+1]-1 of src/dst, with ids local to the graph
@@ -152,6 +176,11 @@ typedef struct truss_run_stats {
   double bytes_support, bytes_lists, bytes_peel;
   /* kernels this call launched (own kernels plus the CUB sort/scan passes) */
   int64_t launches;
+  /* truss_top only: edges of the last candidate subgraph, and how many
+   * candidate subgraphs were decomposed */
+  int64_t candidates;
+  int32_t rounds;
+  int32_t reserved0;
 } truss_run_stats;
 
 /* Statistics of the last successful call on this context. */

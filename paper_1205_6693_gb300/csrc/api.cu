@@ -73,6 +73,16 @@ size_t Arena::reserved() const {
   return s;
 }
 
+std::vector<size_t> Arena::mark() const {
+  std::vector<size_t> m;
+  for (auto &c : chunks_) m.push_back(c.used);
+  return m;
+}
+
+void Arena::rewind(const std::vector<size_t> &m) {
+  for (size_t i = 0; i < chunks_.size(); i++) chunks_[i].used = i < m.size() ? m[i] : 0;
+}
+
 void *Arena::alloc(size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
   if (bytes == 0) bytes = 256;
@@ -381,6 +391,202 @@ int check_common(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, co
   return TRUSS_OK;
 }
 
+// Per-row support and psi (Procedure 6) of the graph the rows define.
+int run_upper_bound(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                    const int32_t *dst, int32_t *support_out, int32_t *psi_out, cudaStream_t s) {
+  TR_CUDA(cudaSetDevice(ctx->device));
+  tr::Arena &A = ctx->arena;
+  A.reset();
+  tr::take_launches();
+  truss_run_stats st{};
+  st.n = n;
+  st.rows = rows;
+  st.graphs = 1;
+  tr::RowsIn in;
+  in.rows = rows;
+  in.n = n;
+  TR_TRY(stage_in(A, src, rows, &in.src, s));
+  TR_TRY(stage_in(A, dst, rows, &in.dst, s));
+  TR_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
+  tr::Csr g;
+  TR_TRY(tr::build_csr(A, in, &g, ctx->d_err, s));
+  st.m = g.m;
+  tr::SupportCfg scfg;
+  scfg.sms = ctx->sms;
+  scfg.pair_cost = ctx->opts.support_pair_cost;
+  scfg.range_work = ctx->opts.support_range_work;
+  scfg.stage_max = ctx->opts.support_stage_max;
+  tr::SupportOut so;
+  TR_TRY(tr::run_support(A, g, scfg, &so, s));
+  st.triangles = so.entries / 3;
+  int32_t *psi = A.get<int32_t>(g.m);
+  if (!psi) return TRUSS_ENOMEM;
+  TR_TRY(tr::compute_psi(A, g, so.sup, psi, s));
+  OutBuf os, op;
+  TR_TRY(stage_out(A, support_out, rows, &os));
+  TR_TRY(stage_out(A, psi_out, rows, &op));
+  TR_TRY(tr::scatter_rows(g, so.sup, psi, os.dev, op.dev, s));
+  TR_TRY(copy_back(os, rows, s));
+  TR_TRY(copy_back(op, rows, s));
+  TR_CUDA(cudaStreamSynchronize(s));
+  st.launches = tr::take_launches();
+  ctx->last = st;
+  return TRUSS_OK;
+}
+
+// Top-t classes (Algorithm 7): supports and psi of the whole graph, then the
+// full pipeline on the candidate subgraph {e : psi(e) >= k_lo}, which gives
+// every truss number >= k_lo exactly (Lemma 2).  k_lo starts at kb - t + 1,
+// kb the largest k with at least k(k-1)/2 edges of psi >= k (a bound on
+// k_max), and is lowered until k_lo <= k_max - t + 1:
+//  * T_{k_lo} empty in the candidate (its k_max' < k_lo): k_max(G) lies in
+//    [k_max', k_lo - 1] (a subgraph's k-trusses lie in the graph's), so
+//    k_lo = k_max' - t + 1 is low enough and that round is the last;
+//  * otherwise k_max = k_max' exactly, and one more round with
+//    k_lo = k_max - t + 1 follows if needed.
+// At most two rounds after the first.
+int run_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+            int32_t t, int32_t *truss_out, int32_t *kmax_out, cudaStream_t s) {
+  TR_CUDA(cudaSetDevice(ctx->device));
+  tr::Arena &A = ctx->arena;
+  A.reset();
+  tr::take_launches();
+  truss_run_stats st{};
+  st.n = n;
+  st.rows = rows;
+  st.graphs = 1;
+  Stage sg{ctx, s};
+  sg.mark();  // 0
+  tr::RowsIn in;
+  in.rows = rows;
+  in.n = n;
+  TR_TRY(stage_in(A, src, rows, &in.src, s));
+  TR_TRY(stage_in(A, dst, rows, &in.dst, s));
+  TR_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
+  tr::Csr g;
+  TR_TRY(tr::build_csr(A, in, &g, ctx->d_err, s));
+  st.m = g.m;
+  tr::SupportCfg scfg;
+  scfg.sms = ctx->sms;
+  scfg.pair_cost = ctx->opts.support_pair_cost;
+  scfg.range_work = ctx->opts.support_range_work;
+  scfg.stage_max = ctx->opts.support_stage_max;
+  tr::SupportOut so;
+  TR_TRY(tr::run_support(A, g, scfg, &so, s));
+  st.triangles = so.entries / 3;
+  int32_t *psi = A.get<int32_t>(g.m), *top = A.get<int32_t>(g.m);
+  int32_t *cs = A.get<int32_t>(g.m), *cd = A.get<int32_t>(g.m), *ce = A.get<int32_t>(g.m);
+  int32_t *phi_rows = A.get<int32_t>(g.m);
+  if (!psi || !top || !cs || !cd || !ce || !phi_rows) return TRUSS_ENOMEM;
+  TR_TRY(tr::compute_psi(A, g, so.sup, psi, s));
+  std::vector<int64_t> cnt_ge;
+  TR_TRY(tr::psi_counts(A, g.m, psi, &cnt_ge, s));
+  sg.mark();  // 1: build, support, psi
+  const int32_t psi_max = (int32_t)cnt_ge.size() - 1;
+  int32_t kmax = 0, thr = 2;
+  int64_t mc = 0;
+  int rounds = 0;
+  tr::PeelResult pr;
+  if (g.m > 0) {
+    // A non-empty k-truss has every vertex of degree >= k-1 in it, hence at
+    // least k(k-1)/2 edges, all with psi >= k: k_max <= kb.
+    int32_t kb = 2;
+    for (int32_t k = psi_max; k > 2; k--)
+      if ((double)cnt_ge[k] >= 0.5 * (double)k * (double)(k - 1)) {
+        kb = k;
+        break;
+      }
+    int32_t k_lo = kb - t + 1 > 2 ? kb - t + 1 : 2;
+    const bool top_trace = getenv("TRUSS_TOP_TRACE") != nullptr;
+    const std::vector<size_t> mk = A.mark();
+    for (;;) {
+      rounds++;
+      A.rewind(mk);
+      TR_TRY(tr::select_candidates(A, g, psi, k_lo, cs, cd, ce, &mc, s));
+      int32_t kc = 0;
+      if (mc > 0) {
+        tr::RowsIn cin;
+        cin.rows = mc;
+        cin.n = g.n;
+        cin.src = cs;
+        cin.dst = cd;
+        tr::Csr gc;
+        TR_TRY(tr::build_csr(A, cin, &gc, ctx->d_err, s));
+        tr::SupportCfg ccfg = scfg;
+        ccfg.records = true;
+        tr::SupportOut sc;
+        TR_TRY(tr::run_support(A, gc, ccfg, &sc, s));
+        int2 *pairs = A.get<int2>(sc.entries);
+        int32_t *truss_e = A.get<int32_t>(gc.m);
+        if (!pairs || !truss_e) return TRUSS_ENOMEM;
+        TR_TRY(tr::run_lists(A, gc, ccfg, sc, pairs, s));
+        tr::PeelCfg pcfg;
+        pcfg.sms = ctx->sms;
+        pcfg.variant = ctx->opts.peel_variant;
+        if (ctx->opts.wait_limit_ns > 0) pcfg.wait_ns = ctx->opts.wait_limit_ns;
+        pr = tr::PeelResult{};
+        int rc = tr::run_peel(A, gc, sc, pairs, pcfg, truss_e, &pr, s);
+        if (rc != TRUSS_OK) return rc;
+        TR_TRY(tr::scatter_rows(gc, sc.sup, truss_e, nullptr, phi_rows, s));
+        kc = pr.kmax;
+      }
+      if (top_trace) {
+        TR_CUDA(cudaStreamSynchronize(s));
+        fprintf(stderr, "truss_top round %d: k_lo %d candidates %lld k_max' %d\n", rounds, k_lo,
+                (long long)mc, kc);
+      }
+      if (k_lo <= 2) {  // the candidate is the whole graph: everything is exact
+        kmax = kc;
+        thr = kmax - t + 1 > 2 ? kmax - t + 1 : 2;
+        break;
+      }
+      if (kc >= k_lo) {
+        kmax = kc;
+        const int32_t need = kmax - t + 1 > 2 ? kmax - t + 1 : 2;
+        if (need >= k_lo) {
+          thr = need;
+          break;
+        }
+        k_lo = need;
+        continue;
+      }
+      // T_{k_lo} is empty: k_max(G) is in [kc, k_lo - 1], so kc - t + 1 is
+      // low enough and the next round is the last
+      const int32_t nk = kc - t + 1 < k_lo ? kc - t + 1 : k_lo - 1;
+      k_lo = nk > 2 ? nk : 2;
+    }
+    TR_TRY(tr::top_classes(g.m, mc, ce, phi_rows, thr, top, s));
+  }
+  sg.mark();  // 2: candidate rounds
+  OutBuf ot;
+  TR_TRY(stage_out(A, truss_out, rows, &ot));
+  TR_TRY(tr::scatter_rows(g, so.sup, top, nullptr, ot.dev, s));
+  TR_TRY(copy_back(ot, rows, s));
+  if (kmax_out) {
+    if (is_device_ptr(kmax_out)) {
+      TR_CUDA(cudaMemcpyAsync(kmax_out, &kmax, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    } else {
+      *kmax_out = kmax;
+    }
+  }
+  sg.mark();  // 3
+  TR_CUDA(cudaStreamSynchronize(s));
+  if (ctx->opts.profile && ctx->have_events) {
+    st.ms_support = sg.ms(0, 1);
+    st.ms_peel = sg.ms(1, 2);
+    st.ms_scatter = sg.ms(2, 3);
+    st.ms_total = sg.ms(0, 3);
+  }
+  st.kmax = kmax;
+  st.levels = pr.levels;
+  st.subrounds = pr.subrounds;
+  st.candidates = mc;
+  st.rounds = rounds;
+  st.launches = tr::take_launches();
+  ctx->last = st;
+  return TRUSS_OK;
+}
+
 }  // namespace
 
 namespace tr {
@@ -490,6 +696,22 @@ int truss_decompose(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
   if (rows > 0 && !truss_out) return TRUSS_EINVAL;
   return run_pipeline(ctx, n, rows, src, dst, 1, nullptr, nullptr, support_out, truss_out,
                       kmax_out, true, (cudaStream_t)cuda_stream);
+}
+
+int truss_upper_bound(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                      const int32_t *dst, int32_t *support_out, int32_t *psi_out,
+                      void *cuda_stream) {
+  TR_TRY(check_common(ctx, n, rows, src, dst));
+  if (rows > 0 && !psi_out) return TRUSS_EINVAL;
+  return run_upper_bound(ctx, n, rows, src, dst, support_out, psi_out,
+                         (cudaStream_t)cuda_stream);
+}
+
+int truss_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+              int32_t t, int32_t *truss_out, int32_t *kmax_out, void *cuda_stream) {
+  TR_TRY(check_common(ctx, n, rows, src, dst));
+  if (t < 1 || (rows > 0 && !truss_out)) return TRUSS_EINVAL;
+  return run_top(ctx, n, rows, src, dst, t, truss_out, kmax_out, (cudaStream_t)cuda_stream);
 }
 
 int truss_decompose_batch(truss_ctx *ctx, int32_t G, const int64_t *n, const int64_t *row_off,

@@ -31,6 +31,10 @@ class Arena {
   size_t reserved() const;
   size_t unused() const;  // bytes of reserved chunks not handed out since reset()
   void release_all();
+  // Allocation state, to hand back everything allocated after it (rewind);
+  // chunks reserved since stay reserved.
+  std::vector<size_t> mark() const;
+  void rewind(const std::vector<size_t> &m);
 
  private:
   struct Chunk {
@@ -140,6 +144,23 @@ int batch_graph_counts(const Csr &g, int32_t G, const int64_t *voff, const int32
                        unsigned long long *m_g, unsigned long long *sup_g, cudaStream_t s);
 
 // Algorithmic byte counts (see the comments in support.cu / peel.cu).
+// ------------------------------------------------------------ top-t ---
+// psi(e) = min{sup(e), x_u, x_v} + 2 of every edge (Procedure 6 with the
+// whole graph as H) (topt.cu).
+int compute_psi(Arena &A, const Csr &g, const int32_t *sup, int32_t *psi, cudaStream_t s);
+// Largest psi and the count of edges with psi >= k for k = 0 .. max psi
+// (host vector, cnt_ge[k]).
+int psi_counts(Arena &A, int64_t m, const int32_t *psi, std::vector<int64_t> *cnt_ge,
+               cudaStream_t s);
+// Edges with psi >= k_lo as rows (u, v) of the relabelled graph and their edge
+// ids; *mc receives their number.
+int select_candidates(Arena &A, const Csr &g, const int32_t *psi, int32_t k_lo, int32_t *cs,
+                      int32_t *cd, int32_t *ce, int64_t *mc, cudaStream_t s);
+// top[e] = phi_rows[r] for candidate r with e = ce[r] if phi_rows[r] >= thr,
+// every other entry 0.
+int top_classes(int64_t m, int64_t mc, const int32_t *ce, const int32_t *phi_rows, int32_t thr,
+                int32_t *top, cudaStream_t s);
+
 int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, double *b_sup,
                         double *b_lists, cudaStream_t s);
 

@@ -53,10 +53,11 @@ class truss_run_stats(ctypes.Structure):
                 ("ms_peel", ctypes.c_float), ("ms_scatter", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("bytes_support", ctypes.c_double),
                 ("bytes_lists", ctypes.c_double), ("bytes_peel", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("rounds", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved0"}
 
 
 class truss_serve_opts(ctypes.Structure):
@@ -96,7 +97,8 @@ _i32 = ctypes.c_int32
 # Symbols declared in include/truss.h (checked by the CPU test suite).
 EXPORTS = ("truss_strerror", "truss_ctx_create", "truss_ctx_set_opts", "truss_ctx_destroy",
            "truss_support",
-           "truss_decompose", "truss_decompose_batch", "truss_last_stats",
+           "truss_decompose", "truss_decompose_batch", "truss_upper_bound", "truss_top",
+           "truss_last_stats",
            "truss_serve_footprint", "truss_serve_start", "truss_serve_submit", "truss_serve_poll",
            "truss_serve_wait", "truss_serve_stop", "truss_support_noalloc")
 
@@ -129,6 +131,10 @@ def _lib():
         L.truss_decompose.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
         L.truss_decompose_batch.restype = ctypes.c_int
         L.truss_decompose_batch.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.truss_upper_bound.restype = ctypes.c_int
+        L.truss_upper_bound.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp]
+        L.truss_top.restype = ctypes.c_int
+        L.truss_top.argtypes = [_vp, _i64, _i64, _vp, _vp, _i32, _vp, _vp, _vp]
         L.truss_last_stats.restype = ctypes.c_int
         L.truss_last_stats.argtypes = [_vp, ctypes.POINTER(truss_run_stats)]
         L.truss_serve_footprint.restype = ctypes.c_int64
@@ -228,6 +234,23 @@ def truss_decompose(ctx, n: int, src, dst, support_out, truss_out, kmax_out=None
     _check(_lib().truss_decompose(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(support_out),
                                   _ptr(truss_out), kp, _stream(stream, src, truss_out)),
            "truss_decompose")
+    return int(k[0]) if kmax_out is None else -1
+
+
+def truss_upper_bound(ctx, n: int, src, dst, support_out, psi_out, stream=None) -> None:
+    rows = _len(src)
+    _check(_lib().truss_upper_bound(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(support_out),
+                                    _ptr(psi_out), _stream(stream, src, psi_out)),
+           "truss_upper_bound")
+
+
+def truss_top(ctx, n: int, src, dst, t: int, truss_out, kmax_out=None, stream=None) -> int:
+    """Returns k_max (also written to kmax_out when given)."""
+    rows = _len(src)
+    k = np.zeros(1, np.int32)
+    kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
+    _check(_lib().truss_top(ctx, n, rows, _ptr(src), _ptr(dst), int(t), _ptr(truss_out), kp,
+                            _stream(stream, src, truss_out)), "truss_top")
     return int(k[0]) if kmax_out is None else -1
 
 
@@ -345,6 +368,12 @@ class Context:
 
     def decompose(self, n, src, dst, support_out, truss_out, kmax_out=None, stream=None):
         return truss_decompose(self.ctx, n, src, dst, support_out, truss_out, kmax_out, stream)
+
+    def upper_bound(self, n, src, dst, support_out, psi_out, stream=None):
+        return truss_upper_bound(self.ctx, n, src, dst, support_out, psi_out, stream)
+
+    def top(self, n, src, dst, t, truss_out, kmax_out=None, stream=None):
+        return truss_top(self.ctx, n, src, dst, t, truss_out, kmax_out, stream)
 
     def decompose_batch(self, n, row_off, src, dst, support_out, truss_out, kmax_out=None,
                         stream=None):
