@@ -9,7 +9,8 @@ input generator package ``graphgen``.
   threaded, with step 2's supports from forward triangle listing.  Wrapped
   here by :func:`truss`; :func:`psi` is the upper bound of Procedure 6
   (Section 6.2) from its definition, and :func:`top` the top-t classes of
-  Algorithm 7 (Section 6.3) read off the full decomposition.
+  Algorithm 7 (Section 6.3) read off the full decomposition; :func:`core`
+  gives vertex core numbers by the bin-sorted degree array.
 * ``checks.py`` -- independent checkers written from the definitions: edge
   subset brute force (Definition 2), the literal Algorithm 1 (Section 3.1),
   triple-enumeration support (Definition 1), core numbers, the upper bound
@@ -57,6 +58,8 @@ def _L():
                                           _i32p, ctypes.c_int64, _i64p, _i32p]
         L.oracle_psi.restype = ctypes.c_int
         L.oracle_psi.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p, _i32p]
+        L.oracle_core.restype = ctypes.c_int
+        L.oracle_core.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p, _i32p]
         L.oracle_check_valid.restype = ctypes.c_int64
         L.oracle_check_valid.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p,
                                          _i32p]
@@ -123,6 +126,21 @@ def top(n: int, src, dst, t: int):
     out = np.where(r.truss >= thr, r.truss, 0).astype(np.int32)
     out[r.truss < 0] = -1
     return out, r.kmax
+
+
+def core(n: int, src, dst):
+    """Core number of every vertex id in [0, n) (0 for isolated vertices) and
+    the largest, by the bin-sorted degree array (see alg2.c)."""
+    src, dst = _c(src), _c(dst)
+    out = np.zeros(max(n, 1), np.int32)
+    k = ctypes.c_int32(0)
+    rc = _L().oracle_core(n, len(src), src.ctypes.data_as(_i32p), dst.ctypes.data_as(_i32p),
+                          out.ctypes.data_as(_i32p), ctypes.byref(k))
+    if rc == -1:
+        raise ValueError("vertex id out of range")
+    if rc:
+        raise MemoryError("oracle_core")
+    return out[:n], k.value
 
 
 def edges(n: int, src, dst):

@@ -353,6 +353,61 @@ int oracle_psi(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
   return OR_OK;
 }
 
+/* Core number of every vertex (the largest k such that v lies in the k-core,
+ * the largest subgraph of minimum degree >= k), by the bin-sorted degree
+ * array that Section 3.2 borrows for its edge bins: vertices sit in an array
+ * ordered by current degree with the start of each degree's block recorded;
+ * the vertex at the front is removed with its current degree as its core
+ * number, and each neighbour of larger current degree moves to the front of
+ * its block, which then starts one later, and loses one degree.
+ * core_out has n entries, indexed by vertex id; *kmax_out = max core. */
+int oracle_core(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+                int32_t *core_out, int32_t *kmax_out) {
+  graph g;
+  int rc = g_build(&g, n, rows, src, dst);
+  if (rc) { g_free(&g); return rc; }
+  int64_t maxd = 0;
+  for (int64_t v = 0; v < n; v++) if (deg(&g, v) > maxd) maxd = deg(&g, v);
+  int64_t *d = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t *start = (int64_t *)calloc((size_t)maxd + 2, sizeof(int64_t));
+  int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int32_t *vert = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  if (!d || !start || !pos || !vert) {
+    free(d); free(start); free(pos); free(vert); g_free(&g);
+    return OR_ENOMEM;
+  }
+  for (int64_t v = 0; v < n; v++) { d[v] = deg(&g, v); start[d[v] + 1]++; }
+  for (int64_t k = 0; k <= maxd; k++) start[k + 1] += start[k];
+  {
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(maxd + 1));
+    if (!fill) { free(d); free(start); free(pos); free(vert); g_free(&g); return OR_ENOMEM; }
+    for (int64_t k = 0; k <= maxd; k++) fill[k] = start[k];
+    for (int64_t v = 0; v < n; v++) { pos[v] = fill[d[v]]++; vert[pos[v]] = (int32_t)v; }
+    free(fill);
+  }
+  int32_t kmax = 0;
+  for (int64_t i = 0; i < n; i++) {
+    int32_t v = vert[i];
+    core_out[v] = (int32_t)d[v];
+    if (d[v] > kmax) kmax = (int32_t)d[v];
+    for (int64_t j = g.off[v]; j < g.off[v + 1]; j++) {
+      int32_t u = g.adj[j];
+      if (d[u] > d[v]) {
+        /* swap u with the first vertex of its block, shrink the block */
+        int64_t du = d[u], pu = pos[u], pw = start[du];
+        int32_t w = vert[pw];
+        if (u != w) { vert[pu] = w; pos[w] = pu; vert[pw] = u; pos[u] = pw; }
+        start[du]++;
+        d[u]--;
+      }
+    }
+  }
+  if (kmax_out) *kmax_out = kmax;
+  free(d); free(start); free(pos); free(vert);
+  g_free(&g);
+  return OR_OK;
+}
+
 /* Edge list in the oracle's canonical order (for tests): eu[e] < ev[e]. */
 int oracle_edges(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
                  int32_t *eu, int32_t *ev, int32_t *row2e, int64_t *m_out) {

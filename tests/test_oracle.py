@@ -342,3 +342,43 @@ def test_sampled_checker_accepts_oracle_and_rejects_mistakes():
     s[sample[3]] += 1
     bad, _ = oracle.check_sample(n, src, dst, r.truss, s, sample)
     assert bad == 1
+
+
+# ------------------------------------------------------------ core numbers
+@pytest.mark.parametrize("seed", range(8))
+def test_core_bins_equal_min_degree_deletion(seed):
+    """oracle.core (bin-sorted degree array, C) against checks.core_numbers
+    (repeated min-degree deletion, Python)."""
+    n = 40 + 9 * seed
+    src, dst = graphgen.er(n, 4 * n, seed=seed)
+    perm = graphgen.permutation(n, seed=seed, stream=1)
+    src, dst = graphgen.add_cliques(src, dst, perm[:12], [5, 7])
+    edges = checks.canonical_edges(src, dst)
+    core, kmax = oracle.core(n, src, dst)
+    want = checks.core_numbers(edges)
+    assert [int(c) for c in core] == [want.get(v, 0) for v in range(n)]
+    assert kmax == max(want.values())
+
+
+def test_core_closed_forms():
+    def core_of(n, edges):
+        s = np.array([a for a, _ in edges], np.int32)
+        d = np.array([b for _, b in edges], np.int32)
+        return [int(x) for x in oracle.core(n, s, d)[0]]
+    assert core_of(7, clique(range(7))) == [6] * 7                       # K_n: n - 1
+    assert core_of(6, [(i, (i + 1) % 6) for i in range(6)]) == [2] * 6   # cycle: 2
+    assert core_of(5, [(i, i + 1) for i in range(4)]) == [1] * 5         # path: 1
+    assert core_of(6, [(0, i) for i in range(1, 6)]) == [1] * 6          # star: 1
+    assert core_of(4, [(0, 1)]) == [1, 1, 0, 0]                          # isolated: 0
+    kab = [(a, b) for a in range(3) for b in range(3, 8)]                # K_{3,5}: 3
+    assert core_of(8, kab) == [3] * 8
+
+
+def test_truss_lies_in_the_core():
+    """Every edge of the k-truss has both endpoints in the (k-1)-core."""
+    n, src, dst = graphgen.tiny()
+    core, _ = oracle.core(n, src, dst)
+    r = oracle.truss(n, src, dst)
+    ok = r.truss > 0
+    assert (core[src[ok]] >= r.truss[ok] - 1).all()
+    assert (core[dst[ok]] >= r.truss[ok] - 1).all()
