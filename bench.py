@@ -358,6 +358,50 @@ def run_top(args, ws, rank, local):
     return 0
 
 
+def run_core(args, ws, rank, local):
+    """Vertex core numbers (truss_core) of the mid graph."""
+    import torch
+    from paper_1205_6693_gb300 import truss as T
+    dev, dist = _dist_init(ws, local)
+    n, src_np, dst_np = graphgen.mid()
+    src = torch.from_numpy(src_np).to(dev)
+    dst = torch.from_numpy(dst_np).to(dev)
+    core = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx = T.Context(local, profile=True)
+    for _ in range(args.warmup):
+        ctx.core(n, src, dst, core, stream=stream)
+    torch.cuda.synchronize(dev)
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kc = ctx.core(n, src, dst, core, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tot += e0.elapsed_time(e1)
+    st = ctx.stats()
+    ctx.close()
+    ms = _max_over_ranks(dist, dev, tot)
+    if rank == 0:
+        line = {"metric": "edges/sec core decomposition (vertex core numbers, bit-exact)",
+                "value": ws * st["m"] * args.steps / (ms / 1e3), "unit": "edges/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "m": st["m"], "n": n, "max_core": kc,
+                           "levels": st["levels"], "subrounds": st["subrounds"],
+                           "stage_ms": {"build": round(st["ms_build"], 3),
+                                        "peel": round(st["ms_peel"], 3)},
+                           "parallelism": f"replicas x{ws}", "l2_flush": True}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_serve(args, ws, rank, local):
     """Served form: Poisson arrivals replayed in real time through the server."""
     import threading
@@ -444,7 +488,7 @@ def main():
                          "smaller scales are profiling cases)")
     ap.add_argument("--no-tune", action="store_true",
                     help="use cached or default schedules; never run the autotuner")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "top"])
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "top", "core"])
     ap.add_argument("--t", type=int, default=10, help="top mode: number of top classes")
     ap.add_argument("--graphs", type=int, default=4096, help="batch mode: graphs")
     ap.add_argument("--window", type=float, default=1.0, help="serve mode: arrival window (s)")
@@ -459,6 +503,8 @@ def main():
         return run_serve(args, ws, rank, local)
     if args.mode == "top":
         return run_top(args, ws, rank, local)
+    if args.mode == "core":
+        return run_core(args, ws, rank, local)
 
     import torch
     from paper_1205_6693_gb300 import truss as T

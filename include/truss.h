@@ -148,6 +148,20 @@ int truss_upper_bound(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *sr
 int truss_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
               int32_t t, int32_t *truss_out, int32_t *kmax_out, void *cuda_stream);
 
+/* ------------------------------------------------------------- k-core --- */
+/* Core number of every vertex: the largest k such that the vertex lies in
+ * the k-core, the largest subgraph in which every vertex has degree >= k.
+ * The paper sets the k-truss against the k-core: a k-truss lies in the
+ * (k-1)-core (Section 1), and Section 7 (Table 6) compares the k_max-truss
+ * with the c_max-core; its edge bins reuse the core decomposition's
+ * bin-sorted degree array (Section 3.2).  This entry point computes the core
+ * decomposition on the same CSR.
+ * core_out: n entries, indexed by vertex id (0 for a vertex without edges);
+ * kmax_out (nullable, host or device int32[1]): the largest core number.
+ * Errors: TRUSS_EINVAL, TRUSS_ENOMEM, TRUSS_ECUDA, TRUSS_ETIMEOUT. */
+int truss_core(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+               int32_t *core_out, int32_t *kmax_out, void *cuda_stream);
+
 /* ------------------------------------------------------------- batched --- */
 /* Decompose G independent graphs in one pass.  Graph g has n[g] vertices and
  * rows row_off[g] .. row_off[g+1]-1 of src/dst, with ids local to the graph

@@ -587,6 +587,57 @@ int run_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const i
   return TRUSS_OK;
 }
 
+// Core numbers of the vertices of the graph the rows define.
+int run_core_numbers(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                     const int32_t *dst, int32_t *core_out, int32_t *kmax_out, cudaStream_t s) {
+  TR_CUDA(cudaSetDevice(ctx->device));
+  tr::Arena &A = ctx->arena;
+  A.reset();
+  tr::take_launches();
+  truss_run_stats st{};
+  st.n = n;
+  st.rows = rows;
+  st.graphs = 1;
+  Stage sg{ctx, s};
+  sg.mark();  // 0
+  tr::RowsIn in;
+  in.rows = rows;
+  in.n = n;
+  TR_TRY(stage_in(A, src, rows, &in.src, s));
+  TR_TRY(stage_in(A, dst, rows, &in.dst, s));
+  TR_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
+  tr::Csr g;
+  TR_TRY(tr::build_csr(A, in, &g, ctx->d_err, s));
+  st.m = g.m;
+  sg.mark();  // 1
+  OutBuf oc;
+  TR_TRY(stage_out(A, core_out, n, &oc));
+  int32_t kmax = 0, levels = 0, subrounds = 0;
+  const long long wait = ctx->opts.wait_limit_ns > 0 ? ctx->opts.wait_limit_ns : 4000000000LL;
+  TR_TRY(tr::run_core(A, g, ctx->sms, wait, oc.dev, &kmax, &levels, &subrounds, s));
+  sg.mark();  // 2
+  TR_TRY(copy_back(oc, n, s));
+  if (kmax_out) {
+    if (is_device_ptr(kmax_out)) {
+      TR_CUDA(cudaMemcpyAsync(kmax_out, &kmax, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    } else {
+      *kmax_out = kmax;
+    }
+  }
+  TR_CUDA(cudaStreamSynchronize(s));
+  if (ctx->opts.profile && ctx->have_events) {
+    st.ms_build = sg.ms(0, 1);
+    st.ms_peel = sg.ms(1, 2);
+    st.ms_total = sg.ms(0, 2);
+  }
+  st.kmax = kmax;
+  st.levels = levels;
+  st.subrounds = subrounds;
+  st.launches = tr::take_launches();
+  ctx->last = st;
+  return TRUSS_OK;
+}
+
 }  // namespace
 
 namespace tr {
@@ -712,6 +763,14 @@ int truss_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const
   TR_TRY(check_common(ctx, n, rows, src, dst));
   if (t < 1 || (rows > 0 && !truss_out)) return TRUSS_EINVAL;
   return run_top(ctx, n, rows, src, dst, t, truss_out, kmax_out, (cudaStream_t)cuda_stream);
+}
+
+int truss_core(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
+               int32_t *core_out, int32_t *kmax_out, void *cuda_stream) {
+  TR_TRY(check_common(ctx, n, rows, src, dst));
+  if (n > 0 && !core_out) return TRUSS_EINVAL;
+  return run_core_numbers(ctx, n, rows, src, dst, core_out, kmax_out,
+                          (cudaStream_t)cuda_stream);
 }
 
 int truss_decompose_batch(truss_ctx *ctx, int32_t G, const int64_t *n, const int64_t *row_off,

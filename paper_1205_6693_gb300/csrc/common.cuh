@@ -109,4 +109,40 @@ __device__ __forceinline__ long long warp_append64(bool pred, unsigned long long
   return (long long)(base + __popc(mask & ((1u << lane_id()) - 1u)));
 }
 
+// Grid-wide barrier of a cooperative launch, with a time limit.  Arrival is
+// one atomic increment of `bar`, a counter that is never reset: the block
+// whose increment returned `old` waits until the counter reaches the next
+// multiple of the grid size (every block arrives exactly once per barrier,
+// so one barrier's arrivals are gridDim.x consecutive values).  A wait longer
+// than wait_ns records TRUSS_ETIMEOUT in *err.  Returns false if any block
+// has recorded an error, so that every block leaves at its next barrier.
+__device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err,
+                                             long long wait_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long old = atomicAdd(bar, 1ull);
+    const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
+    if (old + 1 != target) {
+      volatile unsigned long long *vb = bar;
+      volatile int *verr = err;
+      const unsigned long long t0 = global_ns();
+      int spins = 0;
+      while (*vb < target) {
+        if (++spins > 32) __nanosleep(32);
+        if (*verr != 0) break;
+        if ((long long)(global_ns() - t0) > wait_ns) {
+          atomicExch(err, TRUSS_ETIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = (*(volatile int *)err) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 }  // namespace tr

@@ -161,6 +161,11 @@ int select_candidates(Arena &A, const Csr &g, const int32_t *psi, int32_t k_lo, 
 int top_classes(int64_t m, int64_t mc, const int32_t *ce, const int32_t *phi_rows, int32_t thr,
                 int32_t *top, cudaStream_t s);
 
+// ------------------------------------------------------------- k-core ---
+// Core number of every vertex, written to core_out[input vertex id] (core.cu).
+int run_core(Arena &A, const Csr &g, int sms, long long wait_ns, int32_t *core_out,
+             int32_t *kmax, int32_t *levels, int32_t *subrounds, cudaStream_t s);
+
 int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, double *b_sup,
                         double *b_lists, cudaStream_t s);
 

@@ -97,40 +97,6 @@ struct PeelArgs {
   long long wait_ns;
 };
 
-// Grid-wide barrier with a time limit.  Arrival is one atomic increment of a
-// counter that is never reset: the block whose increment returned `old`
-// waits until the counter reaches the next multiple of the grid size (every
-// block arrives exactly once per barrier, so the arrivals of one barrier are
-// a run of gridDim.x consecutive values).  Returns false if any block has
-// recorded an error (including this barrier timing out).
-__device__ bool grid_barrier(PeelCtl *c, long long wait_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long old = atomicAdd(&c->bar, 1ull);
-    const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
-    if (old + 1 != target) {
-      volatile unsigned long long *vb = &c->bar;
-      volatile int *verr = &c->err;
-      const unsigned long long t0 = global_ns();
-      int spins = 0;
-      while (*vb < target) {
-        if (++spins > 32) __nanosleep(32);
-        if (*verr != 0) break;
-        if ((long long)(global_ns() - t0) > wait_ns) {
-          atomicExch(&c->err, TRUSS_ETIMEOUT);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = (*(volatile int *)&c->err) == 0;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 __device__ __forceinline__ int items_of(int len) { return len > 0 ? (len + kItem - 1) / kItem : 1; }
 
 // Per-warp staging buffers in shared memory (counts are warp-uniform).
@@ -374,7 +340,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
       s_minres = INT_MAX;
       s_live = 0;
     }
-    if (!grid_barrier(ctl, a.wait_ns)) return;
+    if (!grid_barrier(&ctl->bar, &ctl->err, a.wait_ns)) return;
     ph++;
     const int minres = __ldcg(&ctl->minres[slot]);
     const int64_t live = __ldcg(&ctl->live[slot]);
@@ -446,7 +412,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         charge<2 * G>(a, ee, vv, pp, k, s, wb, N, qn, n_dec);
       }
       flush_items(a, wb, N, qn);
-      if (!grid_barrier(ctl, a.wait_ns)) return;
+      if (!grid_barrier(&ctl->bar, &ctl->err, a.wait_ns)) return;
       ph++;
       const int64_t nN = (int64_t)__ldcg(qn);
       s++;

@@ -98,6 +98,7 @@ _i32 = ctypes.c_int32
 EXPORTS = ("truss_strerror", "truss_ctx_create", "truss_ctx_set_opts", "truss_ctx_destroy",
            "truss_support",
            "truss_decompose", "truss_decompose_batch", "truss_upper_bound", "truss_top",
+           "truss_core",
            "truss_last_stats",
            "truss_serve_footprint", "truss_serve_start", "truss_serve_submit", "truss_serve_poll",
            "truss_serve_wait", "truss_serve_stop", "truss_support_noalloc")
@@ -133,6 +134,8 @@ def _lib():
         L.truss_decompose_batch.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.truss_upper_bound.restype = ctypes.c_int
         L.truss_upper_bound.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp]
+        L.truss_core.restype = ctypes.c_int
+        L.truss_core.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp]
         L.truss_top.restype = ctypes.c_int
         L.truss_top.argtypes = [_vp, _i64, _i64, _vp, _vp, _i32, _vp, _vp, _vp]
         L.truss_last_stats.restype = ctypes.c_int
@@ -254,6 +257,16 @@ def truss_top(ctx, n: int, src, dst, t: int, truss_out, kmax_out=None, stream=No
     return int(k[0]) if kmax_out is None else -1
 
 
+def truss_core(ctx, n: int, src, dst, core_out, kmax_out=None, stream=None) -> int:
+    """Core number per vertex into core_out (n entries); returns the largest."""
+    rows = _len(src)
+    k = np.zeros(1, np.int32)
+    kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
+    _check(_lib().truss_core(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(core_out), kp,
+                             _stream(stream, src, core_out)), "truss_core")
+    return int(k[0]) if kmax_out is None else -1
+
+
 def truss_decompose_batch(ctx, n, row_off, src, dst, support_out, truss_out, kmax_out=None,
                           stream=None) -> None:
     """n and row_off are host int64 arrays (G and G+1 entries)."""
@@ -371,6 +384,9 @@ class Context:
 
     def upper_bound(self, n, src, dst, support_out, psi_out, stream=None):
         return truss_upper_bound(self.ctx, n, src, dst, support_out, psi_out, stream)
+
+    def core(self, n, src, dst, core_out, kmax_out=None, stream=None):
+        return truss_core(self.ctx, n, src, dst, core_out, kmax_out, stream)
 
     def top(self, n, src, dst, t, truss_out, kmax_out=None, stream=None):
         return truss_top(self.ctx, n, src, dst, t, truss_out, kmax_out, stream)
