@@ -16,6 +16,10 @@ Decomposition in Massive Networks", without sharing code with ``alg2.c``:
   the (k-1)-core).
 * :func:`psi_upper`         -- the upper bound psi(e) = min{sup(e), x_u, x_v}+2
   of Procedure 6 (Section 6.2) with the whole graph as H.
+* :func:`bottom_up`         -- Algorithm 3 (LowerBounding) and Algorithm 4 with
+  Procedure 5 (Section 5) under an edge budget, with the local truss numbers
+  taken from :func:`truss_alg1`; ``literal_phi2`` selects the reading of
+  Algorithm 3 step 8 (see the function).
 * :func:`invariants`        -- the checks a correct decomposition must pass.
 """
 from __future__ import annotations
@@ -214,3 +218,99 @@ def invariants(edges, sup, phi):
         if S != Tk1:
             bad.append(("maximal", k))
     return bad
+
+
+def _peel_at(edges, pinned, k):
+    """Procedure 5 steps 1-6 on H = edges: repeatedly remove a non-pinned
+    edge with support <= k-2 in what is left; returns the removed edges."""
+    nb = adjacency(edges)
+    key = lambda a, b: (a, b) if a < b else (b, a)  # noqa: E731
+    sup = {e: len(nb[e[0]] & nb[e[1]]) for e in edges}
+    alive = set(edges)
+    removed = set()
+    changed = True
+    while changed:
+        changed = False
+        for e in sorted(alive):
+            if e in pinned or sup[e] > k - 2:
+                continue
+            alive.discard(e)
+            removed.add(e)
+            changed = True
+            u, v = e
+            for w in nb[u] & nb[v]:
+                a, b = key(u, w), key(v, w)
+                if a in alive and b in alive:
+                    sup[a] -= 1
+                    sup[b] -= 1
+            nb[u].discard(v)
+            nb[v].discard(u)
+    return removed
+
+
+def bottom_up(n, edges, budget, literal_phi2=False):
+    """Section 5 under an edge budget.  Algorithm 3: split the vertices into
+    id ranges whose degrees in the current G sum to at most `budget` (one
+    range once G fits; the budget doubles after a pass that removed
+    nothing); for each range's neighbourhood subgraph H every edge keeps
+    max(lower bound, truss number in H) (Lemma 1), and every internal edge
+    leaves G for Phi_2 or G_new.  Step 8's test: with ``literal_phi2`` an
+    internal edge goes to Phi_2 when its support in H is 0; otherwise when
+    its lower bound is still 2.  Algorithm 4: for k = 3, 4, ... (jumping to
+    the smallest bound left), U_k = endpoints of G_new edges with bound <= k,
+    H = NS(U_k) in G_new, and the internal edges Procedure 5 removes at
+    threshold k are Phi_k.  Returns {edge: phi}."""
+    state = {e: 0 for e in edges}
+    lower = {e: 0 for e in edges}
+    phi = {}
+    part_budget, last = budget, -1
+    while True:
+        G = [e for e in edges if state[e] == 0]
+        if not G:
+            break
+        if len(G) == last:
+            part_budget *= 2
+        last = len(G)
+        deg = [0] * n
+        for u, v in G:
+            deg[u] += 1
+            deg[v] += 1
+        if len(G) <= part_budget:
+            parts = [(0, n)]
+        else:
+            parts, acc, a = [], 0, 0
+            for v in range(n):
+                if acc > 0 and acc + deg[v] > part_budget:
+                    parts.append((a, v))
+                    a, acc = v, 0
+                acc += deg[v]
+            parts.append((a, n))
+        for a, b in parts:
+            H = [e for e in G if a <= e[0] < b or a <= e[1] < b]
+            if not H:
+                continue
+            t = truss_alg1(H)
+            nbH = adjacency(H)
+            for e in H:
+                lower[e] = max(lower[e], t[e])
+                if a <= e[0] < b and a <= e[1] < b:
+                    zero = (len(nbH[e[0]] & nbH[e[1]]) == 0) if literal_phi2 else lower[e] <= 2
+                    if zero:
+                        phi[e] = 2
+                        state[e] = 2
+                    else:
+                        state[e] = 1
+    k = 3
+    while True:
+        Gn = [e for e in edges if state[e] == 1]
+        if not Gn:
+            break
+        k = max(k, min(lower[e] for e in Gn))
+        U = {x for e in Gn if lower[e] <= k for x in e}
+        H = [e for e in Gn if e[0] in U or e[1] in U]
+        pinned = {e for e in H if not (e[0] in U and e[1] in U)}
+        for e in _peel_at(H, pinned, k):
+            phi[e] = k
+            state[e] = 2
+        k += 1
+    return phi

@@ -382,3 +382,31 @@ def test_truss_lies_in_the_core():
     ok = r.truss > 0
     assert (core[src[ok]] >= r.truss[ok] - 1).all()
     assert (core[dst[ok]] >= r.truss[ok] - 1).all()
+
+
+# ------------------------------------------- bottom-up under a budget (Sec. 5)
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("budget", [8, 40, 150])
+def test_bottom_up_equals_algorithm2(seed, budget):
+    """Algorithms 3 and 4 (plain Python, local truss numbers by the literal
+    Algorithm 1) against Algorithm 2 on the whole graph."""
+    n = 30 + 6 * seed
+    src, dst = graphgen.er(n, 4 * n, seed=seed)
+    perm = graphgen.permutation(n, seed=seed, stream=1)
+    src, dst = graphgen.add_cliques(src, dst, perm[:13], [5, 8])
+    edges = checks.canonical_edges(src, dst)
+    _, phi, _ = run(edges, n)
+    assert checks.bottom_up(n, edges, budget) == phi
+
+
+def test_bottom_up_step8_reading():
+    """A triangle {0, 1, 2} beside a path 3-...-9, budget 4: the first pass
+    splits the triangle as {0, 1} | {2, 3} and moves (0, 1) to G_new; in the
+    next pass (0, 2) and (1, 2) have support 0 in what is left of G although
+    they lie in a triangle.  Testing the lower bound (3, set in the first
+    pass) keeps them out of Phi_2; testing the support in H would not."""
+    edges = [(0, 1), (0, 2), (1, 2)] + [(i, i + 1) for i in range(3, 9)]
+    _, phi, _ = run(edges, 10)
+    assert checks.bottom_up(10, edges, 4) == phi
+    literal = checks.bottom_up(10, edges, 4, literal_phi2=True)
+    assert phi[(0, 2)] == 3 and literal[(0, 2)] == 2 and literal[(1, 2)] == 2
