@@ -148,6 +148,23 @@ int truss_upper_bound(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *sr
 int truss_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
               int32_t t, int32_t *truss_out, int32_t *kmax_out, void *cuda_stream);
 
+/* ------------------------------------------------ working-set budget --- */
+/* Truss decomposition by the bottom-up method of Section 5 (Algorithm 3
+ * LowerBounding, Algorithm 4, Procedure 5), for graphs whose decomposition
+ * working set (which grows with the number of triangles) does not fit in
+ * device memory.  The canonical edge list stays resident; the in-memory
+ * decomposition only runs on neighbourhood subgraphs (Definition 4) of about
+ * budget_edges edges.  Outputs as truss_decompose (identical values).
+ * truss_last_stats: rounds = neighbourhood subgraphs decomposed, candidates =
+ * the largest one's edges.  A subgraph larger than the budget (one vertex
+ * of higher degree, or a large NS(U_k)) is decomposed whole, so the budget
+ * bounds the working set only as far as the graph allows.
+ * Errors: TRUSS_EINVAL (also budget_edges < 1), TRUSS_ENOMEM, TRUSS_ECUDA,
+ * TRUSS_ETIMEOUT. */
+int truss_decompose_budget(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                           const int32_t *dst, int64_t budget_edges, int32_t *support_out,
+                           int32_t *truss_out, int32_t *kmax_out, void *cuda_stream);
+
 /* ------------------------------------------------------------- k-core --- */
 /* Core number of every vertex: the largest k such that the vertex lies in
  * the k-core, the largest subgraph in which every vertex has degree >= k.
@@ -195,6 +212,9 @@ typedef struct truss_run_stats {
   int64_t candidates;
   int32_t rounds;
   int32_t reserved0;
+  /* peel work (decompositions): triangle-list entries read, residual
+   * decrements, alive-list entries scanned */
+  int64_t peel_entries, peel_decrements, peel_scanned;
 } truss_run_stats;
 
 /* Statistics of the last successful call on this context. */

@@ -329,6 +329,9 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
     st.kmax = pr.kmax;
     st.levels = pr.levels;
     st.subrounds = pr.subrounds;
+    st.peel_entries = (int64_t)pr.entries;
+    st.peel_decrements = (int64_t)pr.decrements;
+    st.peel_scanned = (int64_t)pr.scanned;
   }
 
   OutBuf os, ot;
@@ -389,6 +392,45 @@ int check_common(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, co
   if (rows > 0 && (!src || !dst)) return TRUSS_EINVAL;
   if (rows > 0 && n == 0) return TRUSS_EINVAL;
   return TRUSS_OK;
+}
+
+// The whole pipeline (CSR build, support, lists, peel) on rows already in
+// device memory: per-row support (nullable) and truss number.  Optional:
+// rows whose edges are never removed (pinned_rows) and the last level to run
+// (k_stop); edges not removed by then get truss 0.
+int decompose_device_rows(truss_ctx *ctx, tr::Arena &A, const tr::RowsIn &in, int32_t *sup_rows,
+                          int32_t *truss_rows, const uint8_t *pinned_rows, int32_t k_stop,
+                          tr::PeelResult *pr, cudaStream_t s) {
+  *pr = tr::PeelResult{};
+  if (in.rows == 0) return TRUSS_OK;
+  tr::Csr g;
+  TR_TRY(tr::build_csr(A, in, &g, ctx->d_err, s));
+  tr::SupportCfg cfg;
+  cfg.sms = ctx->sms;
+  cfg.records = true;
+  cfg.pair_cost = ctx->opts.support_pair_cost;
+  cfg.range_work = ctx->opts.support_range_work;
+  cfg.stage_max = ctx->opts.support_stage_max;
+  tr::SupportOut so;
+  TR_TRY(tr::run_support(A, g, cfg, &so, s));
+  int2 *pairs = A.get<int2>(so.entries);
+  int32_t *truss_e = A.get<int32_t>(g.m);
+  if (!pairs || !truss_e) return TRUSS_ENOMEM;
+  TR_TRY(tr::run_lists(A, g, cfg, so, pairs, s));
+  tr::PeelCfg pcfg;
+  pcfg.sms = ctx->sms;
+  pcfg.variant = ctx->opts.peel_variant;
+  if (ctx->opts.wait_limit_ns > 0) pcfg.wait_ns = ctx->opts.wait_limit_ns;
+  pcfg.k_stop = k_stop;
+  if (pinned_rows) {
+    uint8_t *pe = A.get<uint8_t>(g.m);
+    if (!pe) return TRUSS_ENOMEM;
+    TR_TRY(tr::pin_edges(g.rows, g.row2e, pinned_rows, pe, g.m, s));
+    pcfg.pinned = pe;
+  }
+  int rc = tr::run_peel(A, g, so, pairs, pcfg, truss_e, pr, s);
+  if (rc != TRUSS_OK) return rc;
+  return tr::scatter_rows(g, so.sup, truss_e, sup_rows, truss_rows, s);
 }
 
 // Per-row support and psi (Procedure 6) of the graph the rows define.
@@ -510,24 +552,7 @@ int run_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const i
         cin.n = g.n;
         cin.src = cs;
         cin.dst = cd;
-        tr::Csr gc;
-        TR_TRY(tr::build_csr(A, cin, &gc, ctx->d_err, s));
-        tr::SupportCfg ccfg = scfg;
-        ccfg.records = true;
-        tr::SupportOut sc;
-        TR_TRY(tr::run_support(A, gc, ccfg, &sc, s));
-        int2 *pairs = A.get<int2>(sc.entries);
-        int32_t *truss_e = A.get<int32_t>(gc.m);
-        if (!pairs || !truss_e) return TRUSS_ENOMEM;
-        TR_TRY(tr::run_lists(A, gc, ccfg, sc, pairs, s));
-        tr::PeelCfg pcfg;
-        pcfg.sms = ctx->sms;
-        pcfg.variant = ctx->opts.peel_variant;
-        if (ctx->opts.wait_limit_ns > 0) pcfg.wait_ns = ctx->opts.wait_limit_ns;
-        pr = tr::PeelResult{};
-        int rc = tr::run_peel(A, gc, sc, pairs, pcfg, truss_e, &pr, s);
-        if (rc != TRUSS_OK) return rc;
-        TR_TRY(tr::scatter_rows(gc, sc.sup, truss_e, nullptr, phi_rows, s));
+        TR_TRY(decompose_device_rows(ctx, A, cin, nullptr, phi_rows, nullptr, 0, &pr, s));
         kc = pr.kmax;
       }
       if (top_trace) {
@@ -582,6 +607,183 @@ int run_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const i
   st.subrounds = pr.subrounds;
   st.candidates = mc;
   st.rounds = rounds;
+  st.launches = tr::take_launches();
+  ctx->last = st;
+  return TRUSS_OK;
+}
+
+// Bottom-up decomposition under a working-set budget (Section 5).  The
+// canonical edge list of the whole graph stays in device memory (a few
+// bytes per edge); the decomposition pipeline, whose working set grows with
+// the triangles, only ever runs on neighbourhood subgraphs of about `budget`
+// edges.
+//  Algorithm 3: while edges remain in G, split the vertices (in rank order)
+//   into ranges whose degrees in G sum to at most the budget (one range if G
+//   itself fits); decompose each range's neighbourhood subgraph H; every
+//   edge of H keeps max(lower bound, truss number in H) (Lemma 1); each
+//   internal edge leaves G, to Phi_2 if its bound is still 2 and to G_new
+//   otherwise (bottomup.cu explains the reading of step 8).
+//  Algorithm 4 with Procedure 5: for k = 3, 4, ... (skipping k below every
+//   remaining lower bound), U_k = endpoints of G_new edges with lower bound
+//   <= k, H = NS(U_k) in G_new; H is peeled at threshold k with its external
+//   edges pinned, and the internal edges it removes are Phi_k.
+// The supports come from one support pass over the whole graph.
+// Neighbourhood subgraphs larger than the budget (a vertex whose
+// degree alone exceeds it, or an NS(U_k) that does) are decomposed whole.
+int run_bottom_up(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                  const int32_t *dst, int64_t budget, int32_t *support_out, int32_t *truss_out,
+                  int32_t *kmax_out, cudaStream_t s) {
+  TR_CUDA(cudaSetDevice(ctx->device));
+  tr::Arena &A = ctx->arena;
+  A.reset();
+  tr::take_launches();
+  truss_run_stats st{};
+  st.n = n;
+  st.rows = rows;
+  st.graphs = 1;
+  Stage sg{ctx, s};
+  sg.mark();  // 0
+  tr::RowsIn in;
+  in.rows = rows;
+  in.n = n;
+  TR_TRY(stage_in(A, src, rows, &in.src, s));
+  TR_TRY(stage_in(A, dst, rows, &in.dst, s));
+  TR_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), s));
+  tr::Csr g;
+  TR_TRY(tr::build_csr(A, in, &g, ctx->d_err, s));
+  const int64_t m = g.m;
+  st.m = m;
+  // supports of the whole graph: the support pass needs no triangle lists,
+  // so its working set is a few words per edge
+  tr::SupportCfg scfg;
+  scfg.sms = ctx->sms;
+  scfg.pair_cost = ctx->opts.support_pair_cost;
+  scfg.range_work = ctx->opts.support_range_work;
+  scfg.stage_max = ctx->opts.support_stage_max;
+  tr::SupportOut so;
+  TR_TRY(tr::run_support(A, g, scfg, &so, s));
+  st.triangles = so.entries / 3;
+  const int32_t *supx = so.sup;
+  int32_t *lower = A.get<int32_t>(m), *phi = A.get<int32_t>(m);
+  uint8_t *state = A.get<uint8_t>(m), *inU = A.get<uint8_t>(n), *hpin = A.get<uint8_t>(m);
+  int32_t *list = A.get<int32_t>(m), *deg = A.get<int32_t>(n);
+  int32_t *hs = A.get<int32_t>(m), *hd = A.get<int32_t>(m), *hid = A.get<int32_t>(m);
+  int32_t *truss_h = A.get<int32_t>(m);
+  if (!lower || !phi || !state || !inU || !hpin || !list || !deg || !hs || !hd || !hid ||
+      !truss_h)
+    return TRUSS_ENOMEM;
+  TR_CUDA(cudaMemsetAsync(lower, 0, sizeof(int32_t) * (m > 0 ? m : 1), s));
+  TR_CUDA(cudaMemsetAsync(phi, 0, sizeof(int32_t) * (m > 0 ? m : 1), s));
+  TR_CUDA(cudaMemsetAsync(state, 0, (size_t)(m > 0 ? m : 1), s));
+  const std::vector<size_t> mk = A.mark();
+  tr::PeelResult pr;
+  int64_t subgraphs = 0, biggest = 0;
+  std::vector<int32_t> hdeg((size_t)(n > 0 ? n : 1));
+  // ---------------------------------------------------- Algorithm 3 ---
+  // A pass whose ranges all cut every remaining edge leaves G unchanged; the
+  // next pass then doubles the budget of its ranges, so that one range
+  // finally holds all of G.
+  int64_t part_budget = budget, last_nl = -1;
+  for (;;) {
+    int64_t nl = 0;
+    A.rewind(mk);
+    TR_TRY(tr::bu_list_state(A, m, state, 0, list, &nl, s));
+    if (nl == 0) break;
+    if (nl == last_nl) part_budget *= 2;
+    last_nl = nl;
+    TR_TRY(tr::bu_degrees(n, nl, list, g.esrc, g.adjp, deg, s));
+    TR_CUDA(cudaMemcpyAsync(hdeg.data(), deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaStreamSynchronize(s));
+    std::vector<std::pair<int32_t, int32_t>> parts;
+    if (nl <= part_budget) {
+      parts.push_back({0, (int32_t)n});
+    } else {
+      int64_t acc = 0;
+      int32_t a = 0;
+      for (int64_t v = 0; v < n; v++) {
+        if (acc > 0 && acc + hdeg[v] > part_budget) {
+          parts.push_back({a, (int32_t)v});
+          a = (int32_t)v;
+          acc = 0;
+        }
+        acc += hdeg[v];
+      }
+      parts.push_back({a, (int32_t)n});
+    }
+    for (auto &pt : parts) {
+      const std::vector<size_t> mk2 = A.mark();
+      int64_t mh = 0;
+      TR_TRY(tr::bu_select_range(A, nl, list, g.esrc, g.adjp, pt.first, pt.second, hs, hd, hid,
+                                 &mh, s));
+      if (mh == 0) continue;
+      tr::RowsIn hin;
+      hin.rows = mh;
+      hin.n = n;
+      hin.src = hs;
+      hin.dst = hd;
+      TR_TRY(decompose_device_rows(ctx, A, hin, nullptr, truss_h, nullptr, 0, &pr, s));
+      TR_TRY(tr::bu_alg3_update(mh, hid, hs, hd, pt.first, pt.second, truss_h, lower, phi,
+                                state, s));
+      subgraphs++;
+      if (mh > biggest) biggest = mh;
+      A.rewind(mk2);
+    }
+  }
+  // ------------------------------------------- Algorithm 4, Procedure 5 ---
+  // every truss number is at most the largest support + 2: a k beyond that
+  // with edges left in G_new would mean an inconsistency
+  int32_t maxsup = 0;
+  TR_TRY(tr::bu_max(A, m, supx, &maxsup, s));
+  int32_t kmax = 0;
+  for (int32_t k = 3;; k++) {
+    int64_t nl = 0;
+    A.rewind(mk);
+    TR_TRY(tr::bu_list_state(A, m, state, 1, list, &nl, s));
+    if (nl == 0) break;
+    if (k > maxsup + 2) return TRUSS_ECHECK;
+    int32_t mn = 0;
+    TR_TRY(tr::bu_min_lower(A, nl, list, lower, &mn, s));
+    if (mn > k) k = mn;  // U_k is empty below the smallest lower bound
+    if (k > maxsup + 2) return TRUSS_ECHECK;
+    int64_t mh = 0;
+    TR_TRY(tr::bu_select_candidates(A, n, nl, list, g.esrc, g.adjp, lower, k, inU, hs, hd, hid,
+                                    hpin, &mh, s));
+    tr::RowsIn hin;
+    hin.rows = mh;
+    hin.n = n;
+    hin.src = hs;
+    hin.dst = hd;
+    TR_TRY(decompose_device_rows(ctx, A, hin, nullptr, truss_h, hpin, k, &pr, s));
+    TR_TRY(tr::bu_assign(mh, hid, hpin, truss_h, k, phi, state, s));
+    subgraphs++;
+    if (mh > biggest) biggest = mh;
+    kmax = k;
+  }
+  if (kmax == 0 && m > 0) kmax = 2;
+  sg.mark();  // 1
+  OutBuf os, ot;
+  TR_TRY(stage_out(A, support_out, rows, &os));
+  TR_TRY(stage_out(A, truss_out, rows, &ot));
+  TR_TRY(tr::scatter_rows(g, supx, phi, os.dev, ot.dev, s));
+  TR_TRY(copy_back(os, rows, s));
+  TR_TRY(copy_back(ot, rows, s));
+  if (kmax_out) {
+    if (is_device_ptr(kmax_out)) {
+      TR_CUDA(cudaMemcpyAsync(kmax_out, &kmax, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    } else {
+      *kmax_out = kmax;
+    }
+  }
+  sg.mark();  // 2
+  TR_CUDA(cudaStreamSynchronize(s));
+  if (ctx->opts.profile && ctx->have_events) {
+    st.ms_peel = sg.ms(0, 1);
+    st.ms_scatter = sg.ms(1, 2);
+    st.ms_total = sg.ms(0, 2);
+  }
+  st.kmax = kmax;
+  st.candidates = biggest;
+  st.rounds = (int32_t)subgraphs;
   st.launches = tr::take_launches();
   ctx->last = st;
   return TRUSS_OK;
@@ -763,6 +965,15 @@ int truss_top(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const
   TR_TRY(check_common(ctx, n, rows, src, dst));
   if (t < 1 || (rows > 0 && !truss_out)) return TRUSS_EINVAL;
   return run_top(ctx, n, rows, src, dst, t, truss_out, kmax_out, (cudaStream_t)cuda_stream);
+}
+
+int truss_decompose_budget(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src,
+                           const int32_t *dst, int64_t budget_edges, int32_t *support_out,
+                           int32_t *truss_out, int32_t *kmax_out, void *cuda_stream) {
+  TR_TRY(check_common(ctx, n, rows, src, dst));
+  if (budget_edges < 1 || (rows > 0 && !truss_out)) return TRUSS_EINVAL;
+  return run_bottom_up(ctx, n, rows, src, dst, budget_edges, support_out, truss_out, kmax_out,
+                       (cudaStream_t)cuda_stream);
 }
 
 int truss_core(truss_ctx *ctx, int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,

@@ -123,6 +123,10 @@ struct PeelCfg {
   int variant = 0;  // kernel shape (peel.cu: run_peel)
   int sms = 0;
   long long wait_ns = 4000000000LL;
+  // Optional: edges never removed (their triangles still count), and the
+  // last level to run (0 = all).  Edges not removed by then get truss 0.
+  const uint8_t *pinned = nullptr;
+  int k_stop = 0;
 };
 
 struct PeelResult {
@@ -160,6 +164,32 @@ int select_candidates(Arena &A, const Csr &g, const int32_t *psi, int32_t k_lo, 
 // every other entry 0.
 int top_classes(int64_t m, int64_t mc, const int32_t *ce, const int32_t *phi_rows, int32_t thr,
                 int32_t *top, cudaStream_t s);
+
+// ---------------------------------------------------- bottom-up (budget) ---
+// Helpers of the budgeted bottom-up decomposition (bottomup.cu); edge state
+// 0 = in G (Algorithm 3), 1 = in G_new, 2 = truss number known.
+int bu_list_state(Arena &A, int64_t m, const uint8_t *state, int want, int32_t *out,
+                  int64_t *count, cudaStream_t s);
+int bu_degrees(int64_t n, int64_t nl, const int32_t *list, const int32_t *eu, const int32_t *ev,
+               int32_t *deg, cudaStream_t s);
+int bu_select_range(Arena &A, int64_t nl, const int32_t *list, const int32_t *eu,
+                    const int32_t *ev, int32_t va, int32_t vb, int32_t *hs, int32_t *hd,
+                    int32_t *hid, int64_t *mh, cudaStream_t s);
+int bu_alg3_update(int64_t mh, const int32_t *hid, const int32_t *hs, const int32_t *hd,
+                   int32_t va, int32_t vb, const int32_t *truss_h, int32_t *lower, int32_t *phi,
+                   uint8_t *state, cudaStream_t s);
+int bu_min_lower(Arena &A, int64_t nl, const int32_t *list, const int32_t *lower, int32_t *mn,
+                 cudaStream_t s);
+int bu_select_candidates(Arena &A, int64_t n, int64_t nl, const int32_t *list, const int32_t *eu,
+                         const int32_t *ev, const int32_t *lower, int32_t k, uint8_t *inU,
+                         int32_t *hs, int32_t *hd, int32_t *hid, uint8_t *pinned, int64_t *mh,
+                         cudaStream_t s);
+int bu_assign(int64_t mh, const int32_t *hid, const uint8_t *pinned, const int32_t *truss_h,
+              int32_t k, int32_t *phi, uint8_t *state, cudaStream_t s);
+int bu_max(Arena &A, int64_t m, const int32_t *x, int32_t *mx, cudaStream_t s);
+// pinned_e[row2e[r]] = 1 for rows with pinned_rows[r] (others 0).
+int pin_edges(int64_t rows, const int32_t *row2e, const uint8_t *pinned_rows, uint8_t *pinned_e,
+              int64_t m, cudaStream_t s);
 
 // ------------------------------------------------------------- k-core ---
 // Core number of every vertex, written to core_out[input vertex id] (core.cu).

@@ -95,6 +95,7 @@ struct PeelArgs {
   int trace_cap;
   PeelCtl *ctl;
   long long wait_ns;
+  int k_stop;  // last level to run (0 = all)
 };
 
 __device__ __forceinline__ int items_of(int len) { return len > 0 ? (len + kItem - 1) / kItem : 1; }
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   unsigned long long n_entries = 0, n_dec = 0, n_scan = 0;
 
   for (;;) {
+    if (a.k_stop > 0 && k > a.k_stop) break;  // k is the same in every block
     // ------------------------------------------------------------ scan ---
     if (leader && a.trace && ctl->ntrace < a.trace_cap) {
       const unsigned long long t = global_ns();
@@ -445,13 +447,18 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   }
 }
 
-__global__ void k_peel_init(int64_t m, const int32_t *sup, int32_t *res, int32_t *stamp,
-                            int32_t *alive, PeelCtl *ctl) {
+// Residual given to pinned edges: no level ever reaches it, and the
+// decrements it can receive (at most its support) leave it out of reach.
+constexpr int kPinnedRes = INT_MAX / 4;
+
+__global__ void k_peel_init(int64_t m, const int32_t *sup, const uint8_t *pinned, int32_t *res,
+                            int32_t *stamp, int32_t *alive, int32_t *truss, PeelCtl *ctl) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
-    res[e] = sup[e];
+    res[e] = (pinned && pinned[e]) ? kPinnedRes : sup[e];
     stamp[e] = 0;
     alive[e] = (int32_t)e;
+    truss[e] = 0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = 0; i < 3; i++) {
@@ -476,7 +483,8 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
   PeelCtl *ctl = A.get<PeelCtl>(1);
   if (!res || !stamp || !al0 || !al1 || !Q0 || !Q1 || !ctl) return TRUSS_ENOMEM;
   TR_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PeelCtl), s));
-  k_peel_init<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.sup, res, stamp, al0, ctl);
+  k_peel_init<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.sup, cfg.pinned, res, stamp, al0,
+                                                          truss, ctl);
   TR_LAUNCHED();
 
   int dev = 0, sms = cfg.sms;
@@ -513,6 +521,7 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
   a.item_cap = item_cap;
   a.ctl = ctl;
   a.wait_ns = cfg.wait_ns;
+  a.k_stop = cfg.k_stop;
   const char *trace_path = getenv("TRUSS_TRACE");
   const int trace_cap = 1 << 20;
   if (trace_path) {

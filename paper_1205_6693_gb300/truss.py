@@ -54,7 +54,9 @@ class truss_run_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("bytes_support", ctypes.c_double),
                 ("bytes_lists", ctypes.c_double), ("bytes_peel", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("candidates", ctypes.c_int64),
-                ("rounds", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("rounds", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("peel_entries", ctypes.c_int64), ("peel_decrements", ctypes.c_int64),
+                ("peel_scanned", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved0"}
@@ -98,7 +100,7 @@ _i32 = ctypes.c_int32
 EXPORTS = ("truss_strerror", "truss_ctx_create", "truss_ctx_set_opts", "truss_ctx_destroy",
            "truss_support",
            "truss_decompose", "truss_decompose_batch", "truss_upper_bound", "truss_top",
-           "truss_core",
+           "truss_core", "truss_decompose_budget",
            "truss_last_stats",
            "truss_serve_footprint", "truss_serve_start", "truss_serve_submit", "truss_serve_poll",
            "truss_serve_wait", "truss_serve_stop", "truss_support_noalloc")
@@ -134,6 +136,8 @@ def _lib():
         L.truss_decompose_batch.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.truss_upper_bound.restype = ctypes.c_int
         L.truss_upper_bound.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp]
+        L.truss_decompose_budget.restype = ctypes.c_int
+        L.truss_decompose_budget.argtypes = [_vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp]
         L.truss_core.restype = ctypes.c_int
         L.truss_core.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp]
         L.truss_top.restype = ctypes.c_int
@@ -254,6 +258,19 @@ def truss_top(ctx, n: int, src, dst, t: int, truss_out, kmax_out=None, stream=No
     kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
     _check(_lib().truss_top(ctx, n, rows, _ptr(src), _ptr(dst), int(t), _ptr(truss_out), kp,
                             _stream(stream, src, truss_out)), "truss_top")
+    return int(k[0]) if kmax_out is None else -1
+
+
+def truss_decompose_budget(ctx, n: int, src, dst, budget_edges: int, support_out, truss_out,
+                           kmax_out=None, stream=None) -> int:
+    """Returns k_max (also written to kmax_out when given)."""
+    rows = _len(src)
+    k = np.zeros(1, np.int32)
+    kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
+    _check(_lib().truss_decompose_budget(ctx, n, rows, _ptr(src), _ptr(dst), int(budget_edges),
+                                         _ptr(support_out), _ptr(truss_out), kp,
+                                         _stream(stream, src, truss_out)),
+           "truss_decompose_budget")
     return int(k[0]) if kmax_out is None else -1
 
 
@@ -384,6 +401,11 @@ class Context:
 
     def upper_bound(self, n, src, dst, support_out, psi_out, stream=None):
         return truss_upper_bound(self.ctx, n, src, dst, support_out, psi_out, stream)
+
+    def decompose_budget(self, n, src, dst, budget_edges, support_out, truss_out, kmax_out=None,
+                         stream=None):
+        return truss_decompose_budget(self.ctx, n, src, dst, budget_edges, support_out,
+                                      truss_out, kmax_out, stream)
 
     def core(self, n, src, dst, core_out, kmax_out=None, stream=None):
         return truss_core(self.ctx, n, src, dst, core_out, kmax_out, stream)
