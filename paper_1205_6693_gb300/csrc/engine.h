@@ -90,10 +90,11 @@ int build_csr(Arena &A, const RowsIn &in, Csr *out, int32_t *d_err, cudaStream_t
 // ------------------------------------------------------------- support ---
 struct SupportOut {
   int32_t *sup = nullptr;    // [m]  sup(e)
-  int32_t *supA = nullptr;   // [m]  triangles in which e is found from its own tail
+  int32_t *supA = nullptr;   // [m]  triangles in which e is e_uv or e_uw (e in out(u))
   int64_t *toff = nullptr;   // [m+1] triangle-list offsets (exclusive sum of sup)
-  int64_t *wpre = nullptr;   // [m+1] exclusive prefix of the per-edge walk cost
-  int64_t walk = 0;          // total walk cost (entries of out-lists scanned)
+  int64_t walk = 0;          // total walk cost (out-list entries probed, plus fixed costs)
+  int32_t *inedge = nullptr; // [m]  edges grouped by head
+  int64_t *inoff = nullptr;  // [n+1] start of each head's group in inedge
   int64_t entries = 0;       // sum sup = 3 * triangles
   // optional triangle records of the support walk (see support.cu)
   int64_t *tbpre = nullptr;  // [m+1] record-region offsets

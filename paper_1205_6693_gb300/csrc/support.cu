@@ -318,6 +318,214 @@ __device__ __forceinline__ void probe_walk(const SupArgs &a, int64_t bu, const i
   __syncwarp();
 }
 
+// ------------------------------------------------ head-centric support ---
+// The support walk proper: every triangle (u, v, w) with rank u < v < w is
+// found once, from its middle vertex v.  out(v) is staged in shared memory
+// with a hash table of positions (out-lists of more than stage_max entries
+// are searched in global memory instead), and for every in-edge (u, v) the
+// entries of out(u) after v are looked up in it; a hit w at position q of
+// out(v) is the triangle with e_uv = (u, v), e_uw = w's position in out(u)
+// and e_vw = offp[v] + q.  Entries of out(u) after v are exactly the
+// candidates (w must rank above v), so the work of an edge is |out(u) after
+// v| rather than |out(v)|: sum over u of d(d-1)/2 for out-degrees d, which
+// on power-law graphs is a few times smaller than the sum of |out(v)| over
+// the edges (u, v).
+// Counts: supA[e] = triangles in which e is e_uv or e_uw (both in out(u)),
+// supB[e] = triangles in which it is e_vw; sup = supA + supB.
+struct SupVArgs {
+  int64_t n, m;
+  const int64_t *offp;
+  const int32_t *adjp;
+  const int32_t *esrc;
+  const int32_t *inedge;  // [m] edges grouped by head
+  const int32_t *ihead;   // [m] head of inedge[i]
+  const int64_t *inoff;   // [n+1] start of each head's group
+  const int64_t *wpre;    // [m+1] exclusive prefix of the walk cost, in inedge order
+  int64_t W, P;
+  int stage_max;
+  int32_t *supA, *supB;
+  const int64_t *tbpre;  // optional records, as SupArgs
+  int2 *tb;
+  int32_t *cuv;
+};
+
+// Position of w in out(v) (staged: hash table Hs of size 2^(32-sh) over Ls;
+// else a branch-free search of the global list), or -1.
+template <bool STAGED>
+__device__ __forceinline__ int find_in_out(int w, const int32_t *Ls, const unsigned short *Hs,
+                                           int S, int sh, const int32_t *gl, int d) {
+  if (STAGED) {
+    unsigned sl = hslot(w, sh);
+    for (;;) {
+      const int p = Hs[sl];
+      if (p == 0) return -1;
+      if (Ls[p - 1] == w) return p - 1;
+      sl = (sl + 1) & (unsigned)(S - 1);
+    }
+  } else {
+    int q = 0;
+    for (int step = 1 << (31 - __clz(d)); step > 0; step >>= 1) {
+      const int nq = q + step;
+      if (nq <= d && __ldg(&gl[nq - 1]) < w) q = nq;
+    }
+    return (q < d && __ldg(&gl[q]) == w) ? q : -1;
+  }
+}
+
+// The in-edges inedge[i0 .. i1) of head v (bv = offp[v], dv = |out(v)|).
+template <bool STAGED>
+__device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t i1, int64_t bv,
+                                          int dv, int vmax, const int32_t *Ls, int32_t *Cs,
+                                          const unsigned short *Hs, int S, int sh) {
+  const int lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t c0 = i0; c0 < i1; c0 += 32) {
+    const int64_t j = c0 + lane;
+    const bool valid = j < i1;
+    const int e = valid ? __ldg(&a.inedge[j]) : 0;
+    const int u = valid ? __ldg(&a.esrc[e]) : 0;
+    const int64_t uend = valid ? __ldg(&a.offp[u + 1]) : 0;
+    const int len = valid ? (int)(uend - (int64_t)e - 1) : 0;  // entries of out(u) after v
+    const int64_t rb = (valid && a.tb) ? __ldg(&a.tbpre[e]) : 0;
+    const int nv = (int)min((int64_t)32, i1 - c0);
+    for (int o = 0; o < nv; o++) {
+      const int eo = __shfl_sync(TR_FULL, e, o);
+      const int olen = __shfl_sync(TR_FULL, len, o);
+      const int64_t tbase = __shfl_sync(TR_FULL, rb, o);
+      const int64_t start = (int64_t)eo + 1;
+      int cnt = 0;  // triangles of edge eo so far (warp-uniform)
+      for (int t0 = 0; t0 < olen; t0 += 128) {
+        int w[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int t = t0 + k * 32 + lane;
+          w[k] = t < olen ? __ldg(&a.adjp[start + t]) : INT_MAX;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int q =
+              w[k] <= vmax ? find_in_out<STAGED>(w[k], Ls, Hs, S, sh, a.adjp + bv, dv) : -1;
+          const unsigned hm = __ballot_sync(TR_FULL, q >= 0);
+          if (q >= 0) {
+            const int64_t euw = start + t0 + k * 32 + lane;
+            if (STAGED) atomicAdd(&Cs[q], 1);
+            else atomicAdd(&a.supB[bv + q], 1);
+            atomicAdd(&a.supA[euw], 1);
+            if (a.tb)
+              a.tb[tbase + cnt + __popc(hm & lt)] = make_int2((int)euw, (int)(bv + q));
+          }
+          cnt += __popc(hm);
+        }
+        // out(u) is sorted: past max out(v) nothing can match
+        if (__shfl_sync(TR_FULL, w[3], 31) > vmax) break;
+      }
+      if (lane == 0) {
+        if (a.tb) a.cuv[eo] = cnt;
+        if (cnt) atomicAdd(&a.supA[eo], cnt);
+      }
+    }
+  }
+}
+
+// Warps take equal-cost ranges of inedge round-robin; within a range, each
+// head's group is one segment with out(v) staged once.
+__global__ void __launch_bounds__(kBlock, 3) k_support_v(SupVArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  unsigned char *base = smem_raw + (size_t)warp * warp_smem<0>();
+  constexpr int CAP = Cap<0>::value;
+  int32_t *Cs = (int32_t *)base;
+  int32_t *Ls = Cs + CAP;
+  unsigned short *Hs = (unsigned short *)(Ls + CAP);
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = gw; r < a.P; r += nw) {
+    const int64_t ia = lower_bound64(a.wpre, a.m, a.W * r / a.P);
+    const int64_t ib = lower_bound64(a.wpre, a.m, a.W * (r + 1) / a.P);
+    int64_t i = ia;
+    while (i < ib) {
+      const int v = __ldg(&a.ihead[i]);
+      const int64_t vbeg = __ldg(&a.inoff[v]), vend = __ldg(&a.inoff[v + 1]);
+      const int64_t iend = min(ib, vend);
+      const int64_t bv = __ldg(&a.offp[v]);
+      const int dv = (int)(__ldg(&a.offp[v + 1]) - bv);
+      const int64_t i0 = i;
+      i = iend;
+      if (dv == 0) continue;  // no w above v: no triangle has v in the middle
+      const bool whole = i0 == vbeg && iend == vend;
+      if (dv <= a.stage_max) {
+        int lg = 32 - __clz(max(8 * dv - 1, 63));  // ceil(log2(8 dv)), at least 6
+        lg = min(lg, 11);
+        const int S = 1 << lg, sh = 32 - lg;
+        for (int q = lane; q < dv; q += 32) {
+          Ls[q] = __ldg(&a.adjp[bv + q]);
+          Cs[q] = 0;
+        }
+        for (int t = lane; t < S / 2; t += 32) ((uint32_t *)Hs)[t] = 0u;
+        __syncwarp();
+        for (int q = lane; q < dv; q += 32) {
+          unsigned sl = hslot(Ls[q], sh);
+          while (atomicCAS(&Hs[sl], (unsigned short)0, (unsigned short)(q + 1)) != 0)
+            sl = (sl + 1) & (unsigned)(S - 1);
+        }
+        __syncwarp();
+        head_walk<true>(a, i0, iend, bv, dv, Ls[dv - 1], Ls, Cs, Hs, S, sh);
+        __syncwarp();
+        for (int q = lane; q < dv; q += 32) {
+          if (whole) a.supB[bv + q] = Cs[q];
+          else if (Cs[q] != 0) atomicAdd(&a.supB[bv + q], Cs[q]);
+        }
+        __syncwarp();
+      } else {
+        head_walk<false>(a, i0, iend, bv, dv, __ldg(&a.adjp[bv + dv - 1]), nullptr, nullptr,
+                         nullptr, 0, 0);
+      }
+    }
+  }
+}
+
+// Edges grouped by head: counts, then a fill with one cursor per head.
+__global__ void k_head_count(int64_t m, const int32_t *adjp, unsigned long long *cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[adjp[e]], 1ull);
+}
+
+__global__ void k_head_fill(int64_t m, const int32_t *adjp, const int64_t *inoff,
+                            unsigned long long *cur, int32_t *inedge, int32_t *ihead) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int v = adjp[e];
+    const int64_t p = inoff[v] + (int64_t)atomicAdd(&cur[v], 1ull);
+    inedge[p] = (int32_t)e;
+    ihead[p] = v;
+  }
+}
+
+// Head-centric walk cost of inedge[i] = (u, v): |out(u) after v| plus the
+// fixed per-edge cost; and, per edge id, the most triangles it can close as
+// e_uv, min(|out(v)|, |out(u) after v|) (its record region).
+__global__ void k_walk_cost_v(int64_t m, const int64_t *offp, const int32_t *adjp,
+                              const int32_t *esrc, const int32_t *inedge, int64_t *cost,
+                              int64_t *bound, int edge_cost) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i == m) {
+      cost[m] = 0;
+      bound[m] = 0;
+      continue;
+    }
+    const int e = inedge[i];
+    const int64_t after = offp[esrc[e] + 1] - (int64_t)e - 1;
+    cost[i] = after + edge_cost;
+    const int v = adjp[i];
+    const int64_t dv = offp[v + 1] - offp[v];
+    const int u = esrc[i];
+    const int64_t after_i = offp[u + 1] - i - 1;
+    bound[i] = min(dv, after_i);
+  }
+}
+
 // Warps take equal-cost ranges of oriented edges round-robin.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock, MODE == 0 ? 3 : 4) k_support(SupArgs a) {
@@ -593,38 +801,76 @@ int launch_walk(int mode, SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
   return TRUSS_OK;
 }
 
+int launch_walk_v(SupVArgs a, const SupportCfg &cfg, cudaStream_t s) {
+  int dev = 0, sms = cfg.sms;
+  TR_CUDA(cudaGetDevice(&dev));
+  if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t smem = (size_t)(kBlock / 32) * warp_smem<0>();
+  TR_CUDA(cudaFuncSetAttribute(k_support_v, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  int occ = 0;
+  TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_support_v, kBlock, smem));
+  if (occ < 1) occ = 1;
+  const int grid = sms * occ;
+  const int64_t warps = (int64_t)grid * (kBlock / 32);
+  int64_t P = a.W / (cfg.range_work > 0 ? cfg.range_work : kRangeWork);
+  if (P < warps) P = warps;
+  if (P > a.m) P = a.m > 0 ? a.m : 1;
+  a.P = P;
+  const int cap = Cap<0>::value;
+  a.stage_max = cfg.stage_max > 0 && cfg.stage_max < cap ? cfg.stage_max : cap;
+  k_support_v<<<grid, kBlock, smem, s>>>(a);
+  TR_LAUNCHED();
+  return TRUSS_OK;
+}
+
 }  // namespace
 
 int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, cudaStream_t s) {
-  const int64_t m = g.m;
+  const int64_t m = g.m, n = g.n;
   int32_t *supA = A.get<int32_t>(m), *supB = A.get<int32_t>(m), *sup = A.get<int32_t>(m);
   int64_t *sup64 = A.get<int64_t>(m + 1), *toff = A.get<int64_t>(m + 1);
   int64_t *wcost = A.get<int64_t>(m + 1), *wpre = A.get<int64_t>(m + 1);
   int64_t *wbound = A.get<int64_t>(m + 1), *tbpre = A.get<int64_t>(m + 1);
-  if (!supA || !supB || !sup || !sup64 || !toff || !wcost || !wpre || !wbound || !tbpre)
+  unsigned long long *hcnt = A.get<unsigned long long>(n + 1);
+  int64_t *inoff = A.get<int64_t>(n + 1);
+  int32_t *inedge = A.get<int32_t>(m), *ihead = A.get<int32_t>(m);
+  if (!supA || !supB || !sup || !sup64 || !toff || !wcost || !wpre || !wbound || !tbpre ||
+      !hcnt || !inoff || !inedge || !ihead)
     return TRUSS_ENOMEM;
   TR_CUDA(cudaMemsetAsync(supA, 0, sizeof(int32_t) * m, s));
   TR_CUDA(cudaMemsetAsync(supB, 0, sizeof(int32_t) * m, s));
   int64_t W = 0, R = 0;
   if (m > 0) {
-    k_walk_cost<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, g.offp, g.adjp, g.esrc, wcost,
-                                                                wbound, cfg.pair_cost > 0 ? cfg.pair_cost : cfg.pair_cost < 0 ? 0 : kEdgeCost);
+    // edges grouped by head
+    TR_CUDA(cudaMemsetAsync(hcnt, 0, sizeof(unsigned long long) * (n + 1), s));
+    k_head_count<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, g.adjp, hcnt);
     TR_LAUNCHED();
     size_t tb = 0;
-    TR_TRY(exclusive_sum_i64(nullptr, &tb, wcost, wpre, m + 1, s));
-    void *tmp = A.alloc(tb);
+    TR_TRY(exclusive_sum_i64(nullptr, &tb, (const int64_t *)hcnt, inoff, n + 1, s));
+    size_t tb2 = 0;
+    TR_TRY(exclusive_sum_i64(nullptr, &tb2, wcost, wpre, m + 1, s));
+    void *tmp = A.alloc(tb > tb2 ? tb : tb2);
     if (!tmp) return TRUSS_ENOMEM;
-    TR_TRY(exclusive_sum_i64(tmp, &tb, wcost, wpre, m + 1, s));
-    if (cfg.records) TR_TRY(exclusive_sum_i64(tmp, &tb, wbound, tbpre, m + 1, s));
+    TR_TRY(exclusive_sum_i64(tmp, &tb, (const int64_t *)hcnt, inoff, n + 1, s));
+    TR_CUDA(cudaMemsetAsync(hcnt, 0, sizeof(unsigned long long) * (n + 1), s));
+    k_head_fill<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, g.adjp, inoff, hcnt, inedge, ihead);
+    TR_LAUNCHED();
+    const int ec = cfg.pair_cost > 0 ? cfg.pair_cost : cfg.pair_cost < 0 ? 0 : kEdgeCost;
+    k_walk_cost_v<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, g.offp, g.adjp, g.esrc,
+                                                                  inedge, wcost, wbound, ec);
+    TR_LAUNCHED();
+    tb2 = tb > tb2 ? tb : tb2;
+    TR_TRY(exclusive_sum_i64(tmp, &tb2, wcost, wpre, m + 1, s));
+    if (cfg.records) TR_TRY(exclusive_sum_i64(tmp, &tb2, wbound, tbpre, m + 1, s));
     TR_CUDA(cudaMemcpyAsync(&W, wpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (cfg.records)
       TR_CUDA(cudaMemcpyAsync(&R, tbpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TR_CUDA(cudaStreamSynchronize(s));
   }
   // Records need 8 R bytes now and the lists later at most 24 R more, plus
-  // 16 m for the head-ordered edge index of the second list pass; use them
-  // only when that fits in free device memory (else the list pass walks the
-  // graph a second time).
+  // a few words per edge for the list passes; use them only when that fits
+  // in free device memory (else the list pass walks the graph a second time).
   int2 *recs = nullptr;
   int32_t *cuv = nullptr;
   if (cfg.records && R > 0) {
@@ -646,12 +892,15 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
     }
   }
   if (W > 0) {
-    SupArgs a{};
-    a.n = g.n;
+    SupVArgs a{};
+    a.n = n;
     a.m = m;
     a.offp = g.offp;
     a.adjp = g.adjp;
     a.esrc = g.esrc;
+    a.inedge = inedge;
+    a.ihead = ihead;
+    a.inoff = inoff;
     a.wpre = wpre;
     a.W = W;
     a.supA = supA;
@@ -659,7 +908,7 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
     a.tbpre = tbpre;
     a.tb = recs;
     a.cuv = cuv;
-    TR_TRY(launch_walk(0, a, cfg, s));
+    TR_TRY(launch_walk_v(a, cfg, s));
   }
   k_sum<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, supA, supB, sup, sup64);
   TR_LAUNCHED();
@@ -674,9 +923,10 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
   out->sup = sup;
   out->supA = supA;
   out->toff = toff;
-  out->wpre = wpre;
   out->walk = W;
   out->entries = total;
+  out->inedge = inedge;
+  out->inoff = inoff;
   out->tbpre = recs ? tbpre : nullptr;
   out->tb = recs;
   out->cuv = recs ? cuv : nullptr;
@@ -694,19 +944,8 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
     TR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     k_cursors_rec<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.cuv, cur);
     TR_LAUNCHED();
-    // head-ordered index of the oriented edges for pass 2
-    uint32_t *hk = A.get<uint32_t>(m);
-    int32_t *ids = A.get<int32_t>(m), *inedge = A.get<int32_t>(m);
-    if (!hk || !ids || !inedge) return TRUSS_ENOMEM;
-    k_edge_ids<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, ids);
-    TR_LAUNCHED();
-    const int vb = bits_for(g.n > 1 ? (uint64_t)(g.n - 1) : 1);
-    size_t tbytes = 0;
-    TR_TRY(sort_pairs_u32(nullptr, &tbytes, (const uint32_t *)g.adjp, hk, ids, inedge, m, 0, vb,
-                          s));
-    void *tmp = A.alloc(tbytes);
-    if (!tmp) return TRUSS_ENOMEM;
-    TR_TRY(sort_pairs_u32(tmp, &tbytes, (const uint32_t *)g.adjp, hk, ids, inedge, m, 0, vb, s));
+    // pass 2 walks the edges grouped by head (the support walk's index)
+    const int32_t *inedge = so.inedge;
     int dev = 0, sms = cfg.sms;
     TR_CUDA(cudaGetDevice(&dev));
     if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -721,10 +960,26 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
     TR_CUDA(cudaStreamSynchronize(s));
     return h_err != 0 ? TRUSS_ECHECK : TRUSS_OK;
   }
+  // No records (short of memory): walk the graph again, owner by owner, and
+  // write the lists directly.  Its ranges need the owner-centric walk cost.
   unsigned long long *curA = A.get<unsigned long long>(m), *curB = A.get<unsigned long long>(m);
+  int64_t *wcost = A.get<int64_t>(m + 1), *wpre = A.get<int64_t>(m + 1);
+  int64_t *wbound = A.get<int64_t>(m + 1);
   int *err = A.get<int>(1);
-  if (!curA || !curB || !err) return TRUSS_ENOMEM;
+  if (!curA || !curB || !wcost || !wpre || !wbound || !err) return TRUSS_ENOMEM;
   TR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  const int ec = cfg.pair_cost > 0 ? cfg.pair_cost : cfg.pair_cost < 0 ? 0 : kEdgeCost;
+  k_walk_cost<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, g.offp, g.adjp, g.esrc, wcost,
+                                                              wbound, ec);
+  TR_LAUNCHED();
+  size_t tb = 0;
+  TR_TRY(exclusive_sum_i64(nullptr, &tb, wcost, wpre, m + 1, s));
+  void *tmp = A.alloc(tb);
+  if (!tmp) return TRUSS_ENOMEM;
+  TR_TRY(exclusive_sum_i64(tmp, &tb, wcost, wpre, m + 1, s));
+  int64_t W = 0;
+  TR_CUDA(cudaMemcpyAsync(&W, wpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TR_CUDA(cudaStreamSynchronize(s));
   k_cursors<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.supA, curA, curB);
   TR_LAUNCHED();
   SupArgs a{};
@@ -733,8 +988,8 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
   a.offp = g.offp;
   a.adjp = g.adjp;
   a.esrc = g.esrc;
-  a.wpre = so.wpre;
-  a.W = so.walk;
+  a.wpre = wpre;
+  a.W = W;
   a.supA = so.supA;
   a.curA = curA;
   a.curB = curB;
@@ -753,45 +1008,40 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
 namespace tr {
 
 namespace {
-// Bytes the support walk must move, independent of caching: per owner u with
-// d = |out(u)| >= 2, its two offsets (16 B), out(u) read (4d) and the owner
-// counts stored (4d); per walked edge (u, v) (all but the last of out(u)),
-// v's two offsets (16 B) and out(v) (4 |out(v)|).
-__global__ void k_count_walk(int64_t n, const int64_t *offp, const int32_t *adjp,
-                             unsigned long long *acc) {
+
+// Algorithmic bytes of the head-centric walk, summed over vertices w (the
+// out-degree d = |out(w)|): as a head, out(w) is staged and its counts are
+// stored (16 + 8d, when d >= 1); as a tail, each out-edge at position i
+// costs its index, tail and offsets (24 B) and the read of the d - i - 1
+// entries after it (4 B each), 24d + 2d(d-1) in all.
+__global__ void k_count_walk(int64_t n, const int64_t *offp, unsigned long long *acc) {
   unsigned long long local = 0;
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
-       u += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t bu = offp[u], d = offp[u + 1] - bu;
-    if (d < 2) continue;
-    local += 16ull + 8ull * (unsigned long long)d;
-    for (int64_t i = 0; i < d - 1; i++) {
-      const int v = adjp[bu + i];
-      local += 16ull + 4ull * (unsigned long long)(offp[v + 1] - offp[v]);
-    }
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long d = (unsigned long long)(offp[w + 1] - offp[w]);
+    if (d == 0) continue;
+    local += 16ull + 8ull * d + 24ull * d + 2ull * d * (d - 1);
   }
   for (int o = 16; o >= 1; o >>= 1) local += __shfl_down_sync(TR_FULL, local, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(acc, local);
 }
 }  // namespace
 
-// Algorithmic bytes of the support pass: walk bytes + 8 B per triangle (the
-// read-modify-write of supB).  Of the list pass: walk bytes + 60 B per
-// triangle (three 8-B list entries written, three 8-B list offsets and one
-// 4-B owner count read, one 8-B cursor read-modify-write).
+// Algorithmic bytes of the support pass: walk bytes + per triangle the
+// read-modify-write of e_uw's count (8 B) and, when recording, its 8-B
+// record.  Of the list pass: see below.
 int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, double *b_sup,
                         double *b_lists, cudaStream_t s) {
   unsigned long long *acc = A.get<unsigned long long>(1);
   if (!acc) return TRUSS_ENOMEM;
   TR_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
   if (g.n > 0 && g.m > 0) {
-    k_count_walk<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, g.offp, g.adjp, acc);
+    k_count_walk<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, g.offp, acc);
     TR_LAUNCHED();
   }
   unsigned long long h = 0;
   TR_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
   TR_CUDA(cudaStreamSynchronize(s));
-  // per triangle: the (v, w) count RMW, plus the 8-B record when recording;
   // lists from records: the record read by both passes, three entries, two
   // cursor RMWs (56 B), and per edge the cursor set-up and both passes'
   // offset/count reads (56 B; the head-order sort is not counted); lists by
