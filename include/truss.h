@@ -89,7 +89,11 @@ typedef struct truss_opts {
    * the support walk is split into equal-cost ranges (0 = 64, negative =
    * none). */
   int32_t support_pair_cost;
-  int32_t reserved[7];
+  /* Non-zero: build the triangle lists by a second walk of the graph, the
+   * path taken anyway when the support walk's triangle records do not fit
+   * in free device memory (0 = records whenever they fit). */
+  int32_t lists_by_walk;
+  int32_t reserved[6];
 } truss_opts;
 
 /* Create a context bound to CUDA device `device` (ordinal).  opts may be NULL

@@ -288,7 +288,7 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
 
   tr::SupportCfg scfg;
   scfg.sms = ctx->sms;
-  scfg.records = want_truss;
+  scfg.records = want_truss && !ctx->opts.lists_by_walk;
   scfg.pair_cost = ctx->opts.support_pair_cost;
   scfg.range_work = ctx->opts.support_range_work;
   scfg.stage_max = ctx->opts.support_stage_max;

@@ -232,92 +232,6 @@ __device__ __forceinline__ unsigned hslot(int w, int sh) {
   return ((unsigned)w * 0x9E3779B1u) >> sh;
 }
 
-// MODE 0 with out(u) staged (Ls, d entries): the triangles of the edges
-// (u, Ls[i]) for i in [i0, i1).  out(u) goes into a hash table Hs of
-// positions + 1 (linear probing, load factor <= 1/4); each entry w of out(v)
-// is looked up there, and a hit at position q is the triangle (u, v, w) with
-// e_uv = bu + i, e_uw = bu + q and e_vw = w's position in adjp.  Every such
-// w ranks above v, so nothing outside out(u) after v can match.  A triangle
-// adds 1 to supB[e_vw] and to Cs[q] (e_uw's owner count), and the pair's
-// total goes to Cs[i]; with records on, the triangle is written as
-// (e_uw, e_vw) to e_uv's record region, its index inside the region taken
-// from a warp ballot.
-__device__ __forceinline__ void probe_walk(const SupArgs &a, int64_t bu, const int32_t *Ls,
-                                           int d, int32_t *Cs, unsigned short *Hs, int i0,
-                                           int i1) {
-  const int lane = lane_id();
-  const unsigned lt = (1u << lane) - 1u;
-  int lg = 32 - __clz(max(8 * d - 1, 63));  // ceil(log2(8 d)), at least 6
-  lg = min(lg, 11);
-  const int S = 1 << lg, sh = 32 - lg;
-  for (int t = lane; t < S / 2; t += 32) ((uint32_t *)Hs)[t] = 0u;
-  __syncwarp();
-  for (int q = lane; q < d; q += 32) {
-    unsigned sl = hslot(Ls[q], sh);
-    while (atomicCAS(&Hs[sl], (unsigned short)0, (unsigned short)(q + 1)) != 0)
-      sl = (sl + 1) & (unsigned)(S - 1);
-  }
-  __syncwarp();
-  const int Lmax = Ls[d - 1];
-  for (int c0 = i0; c0 < i1; c0 += 32) {
-    // offsets (and record bases) of 32 pairs at once
-    const int i = c0 + lane;
-    const bool valid = i < i1;
-    const int v = valid ? Ls[i] : 0;
-    const int64_t vb = valid ? __ldg(&a.offp[v]) : 0;
-    const int len = valid ? (int)(__ldg(&a.offp[v + 1]) - vb) : 0;
-    const int64_t rb = (valid && a.tb) ? __ldg(&a.tbpre[bu + i]) : 0;
-    const int nv = min(32, i1 - c0);
-    for (int o = 0; o < nv; o++) {
-      const int64_t ob = __shfl_sync(TR_FULL, vb, o);
-      const int olen = __shfl_sync(TR_FULL, len, o);
-      const int64_t tbase = __shfl_sync(TR_FULL, rb, o);
-      const int io = c0 + o;
-      int cnt = 0;  // triangles of this pair so far (warp-uniform)
-      for (int t0 = 0; t0 < olen; t0 += 128) {
-        int w[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const int t = t0 + k * 32 + lane;
-          w[k] = t < olen ? __ldg(&a.adjp[ob + t]) : INT_MAX;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          int q = -1;
-          if (w[k] <= Lmax) {
-            unsigned sl = hslot(w[k], sh);
-            for (;;) {
-              const int p = Hs[sl];
-              if (p == 0) break;
-              if (Ls[p - 1] == w[k]) {
-                q = p - 1;
-                break;
-              }
-              sl = (sl + 1) & (unsigned)(S - 1);
-            }
-          }
-          const unsigned hm = __ballot_sync(TR_FULL, q >= 0);
-          if (q >= 0) {
-            const int64_t evw = ob + t0 + k * 32 + lane;
-            atomicAdd(&a.supB[evw], 1);
-            atomicAdd(&Cs[q], 1);
-            if (a.tb)
-              a.tb[tbase + cnt + __popc(hm & lt)] = make_int2((int)(bu + q), (int)evw);
-          }
-          cnt += __popc(hm);
-        }
-        // out(v) is sorted: once an entry exceeds max out(u), none later can match
-        if (__shfl_sync(TR_FULL, w[3], 31) > Lmax) break;
-      }
-      if (lane == 0) {
-        if (a.tb) a.cuv[bu + io] = cnt;
-        if (cnt) atomicAdd(&Cs[io], cnt);
-      }
-    }
-  }
-  __syncwarp();
-}
-
 // ------------------------------------------------ head-centric support ---
 // The support walk proper: every triangle (u, v, w) with rank u < v < w is
 // found once, from its middle vertex v.  out(v) is staged in shared memory
@@ -536,8 +450,7 @@ __global__ void __launch_bounds__(kBlock, MODE == 0 ? 3 : 4) k_support(SupArgs a
   // layout: counters/cursors (8-byte aligned first), then L, then the out(v) chunk
   void *Cs = base;
   int32_t *Ls = (int32_t *)(base + (size_t)CAP * (MODE == 0 ? 4 : 8));
-  unsigned short *Hs = (unsigned short *)(Ls + CAP);  // MODE 0 staged owners
-  int32_t *Abuf = Ls + CAP;                           // merge path
+  int32_t *Abuf = Ls + CAP;  // out(v) chunk of the merge path
   __shared__ int s_uvc[kBlock / 32];
   int *uvc = &s_uvc[warp];
   if (lane == 0) *uvc = 0;
@@ -569,12 +482,8 @@ __global__ void __launch_bounds__(kBlock, MODE == 0 ? 3 : 4) k_support(SupArgs a
         __syncwarp();
         C = Cs;
         if (MODE == 1 && !whole) C = a.curA + bu;  // cursors shared by several ranges
-        if (MODE == 0) {
-          probe_walk(a, bu, Ls, d, (int32_t *)Cs, Hs, i0, i1);
-        } else {
-          OutList<true> ol{Ls, d};
-          walk<MODE, true>(a, bu, ol, C, i0, i1, Abuf, uvc);
-        }
+        OutList<true> ol{Ls, d};
+        walk<MODE, true>(a, bu, ol, C, i0, i1, Abuf, uvc);
       } else {
         C = MODE == 0 ? (void *)(a.supA + bu) : (void *)(a.curA + bu);
         OutList<false> ol{a.adjp + bu, d};
@@ -769,23 +678,19 @@ __global__ void k_cursors(int64_t m, const int64_t *toff, const int32_t *supA,
   }
 }
 
-int launch_walk(int mode, SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
+// The owner-centric list walk (k_support<1>), used when the triangle
+// records do not fit.
+int launch_list_walk(SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
   int dev = 0, sms = cfg.sms;
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const size_t smem = (size_t)(kBlock / 32) * (mode == 0 ? warp_smem<0>() : warp_smem<1>());
+  const size_t smem = (size_t)(kBlock / 32) * warp_smem<1>();
   // the per-warp buffers (dynamic) plus small static counters exceed the
   // default 48 KB window: opt in to the larger per-block limit
-  TR_CUDA(cudaFuncSetAttribute(k_support<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kBlock / 32 * warp_smem<0>())));
   TR_CUDA(cudaFuncSetAttribute(k_support<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kBlock / 32 * warp_smem<1>())));
+                               (int)smem));
   int occ = 0;
-  if (mode == 0) {
-    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_support<0>, kBlock, smem));
-  } else {
-    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_support<1>, kBlock, smem));
-  }
+  TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_support<1>, kBlock, smem));
   if (occ < 1) occ = 1;
   const int grid = sms * occ;
   const int64_t warps = (int64_t)grid * (kBlock / 32);
@@ -793,10 +698,9 @@ int launch_walk(int mode, SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
   if (P < warps) P = warps;
   if (P > a.m) P = a.m > 0 ? a.m : 1;
   a.P = P;
-  const int cap = mode == 0 ? Cap<0>::value : Cap<1>::value;
+  const int cap = Cap<1>::value;
   a.stage_max = cfg.stage_max > 0 && cfg.stage_max < cap ? cfg.stage_max : cap;
-  if (mode == 0) k_support<0><<<grid, kBlock, smem, s>>>(a);
-  else k_support<1><<<grid, kBlock, smem, s>>>(a);
+  k_support<1><<<grid, kBlock, smem, s>>>(a);
   TR_LAUNCHED();
   return TRUSS_OK;
 }
@@ -996,7 +900,7 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
   a.pairs = pairs;
   a.entries = so.entries;
   a.err = err;
-  TR_TRY(launch_walk(1, a, cfg, s));
+  TR_TRY(launch_list_walk(a, cfg, s));
   int h_err = 0;
   TR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   TR_CUDA(cudaStreamSynchronize(s));

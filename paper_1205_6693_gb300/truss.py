@@ -41,7 +41,8 @@ class truss_opts(ctypes.Structure):
     _fields_ = [("wait_limit_ns", ctypes.c_int64), ("profile", ctypes.c_int32),
                 ("count_bytes", ctypes.c_int32), ("support_stage_max", ctypes.c_int32),
                 ("peel_variant", ctypes.c_int32), ("support_range_work", ctypes.c_int32),
-                ("support_pair_cost", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("support_pair_cost", ctypes.c_int32), ("lists_by_walk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class truss_run_stats(ctypes.Structure):

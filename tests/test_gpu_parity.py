@@ -274,3 +274,16 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         assert_same(c2, n, src, dst)
     finally:
         c2.close()
+
+
+def test_lists_by_second_walk():
+    """The list builder taken when the triangle records do not fit (a second,
+    owner-centric walk), forced through truss_opts.lists_by_walk."""
+    from paper_1205_6693_gb300 import truss as T
+    c = T.Context(0, lists_by_walk=1)
+    try:
+        for n, src, dst in (graphgen.tiny(),
+                            (1 << 13, *graphgen.rmat_raw(13, 16 << 13, seed=4))):
+            assert_same(c, n, src, dst)
+    finally:
+        c.close()
