@@ -400,8 +400,10 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         for (int g = 0; g < G; g++) {
           const bool ha = j < cnt[g], hb = j + 8 < cnt[g];
           r[g] = ha ? __ldcg(&a.res[ee[2 * g]]) : 0;
-          pp[2 * g] = ha ? __ldg(&a.pairs[lb[g] + j]) : make_int2(0, 0);
-          pp[2 * g + 1] = hb ? __ldg(&a.pairs[lb[g] + j + 8]) : make_int2(0, 0);
+          // list entries are read once: evict-first, so that the residuals
+          // and stamps (re-read at random) keep their place in L2
+          pp[2 * g] = ha ? __ldcs(&a.pairs[lb[g] + j]) : make_int2(0, 0);
+          pp[2 * g + 1] = hb ? __ldcs(&a.pairs[lb[g] + j + 8]) : make_int2(0, 0);
           vv[2 * g] = ha;
           vv[2 * g + 1] = hb;
         }
