@@ -88,8 +88,8 @@ def traffic_for(stage: str):
             parts = line.split()
             if parts[0] == "csrc_sha256":
                 sha = parts[1]
-            elif len(parts) >= 4:
-                rows[parts[0]] = int(parts[2]) + int(parts[3])
+            elif len(parts) >= 4:  # a stage may run several kernels: add them up
+                rows[parts[0]] = rows.get(parts[0], 0) + int(parts[2]) + int(parts[3])
     if sha != csrc_sha256():
         return None
     return rows.get(stage)
@@ -674,8 +674,8 @@ def main():
     dom = max(cand, key=lambda k: cand[k][0])
     dms, dbytes = cand[dom]
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
-    kernel_name = {"support": "k_support<0>",
-                   "lists": "k_lists_from_records",
+    kernel_name = {"support": "k_support_v",
+                   "lists": "k_lists_from_records + k_lists_vw",
                    "peel": "k_peel (persistent, cooperative)"}[dom]
     traffic = traffic_for(dom) if args.rmat_scale == 20 else None
 
