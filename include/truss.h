@@ -80,7 +80,9 @@ typedef struct truss_opts {
   int32_t support_stage_max;
   /* Peel kernel variant: 0 or 2 = two 512-thread blocks per SM, one work item
    * per lane group; 1 = one block per SM, two items per lane group; 3 = one
-   * block per SM, one item. */
+   * block per SM, one item; 4 = the barrier-free peel (a destroyed bit per
+   * triangle and a work queue per level instead of sub-rounds; it needs the
+   * triangle records and fewer than 2^32 of them, else variant 0 runs). */
   int32_t peel_variant;
   /* Target walk cost (out-list entries) of one warp range of the support
    * walk (0 = 16384). */

@@ -35,14 +35,14 @@ SPACE: dict[str, tuple[int, ...]] = {
     "support_range_work": (0, 4096, 8192, 32768, 65536),
     "support_stage_max": (0, 64, 128, 256),
     "support_pair_cost": (0, 16, 32, 128, 256),
-    "peel_variant": (0, 1, 3),
+    "peel_variant": (0, 1, 3, 4),
 }
 # Stage-time keys of truss_last_stats each knob is judged on.
 OBJECTIVE: dict[str, tuple[str, ...]] = {
     "support_range_work": ("ms_support", "ms_lists"),
     "support_stage_max": ("ms_support", "ms_lists"),
     "support_pair_cost": ("ms_support", "ms_lists"),
-    "peel_variant": ("ms_peel",),
+    "peel_variant": ("ms_lists", "ms_peel"),  # variant 4 also changes the list pass
 }
 
 _lock = threading.Lock()

@@ -317,13 +317,19 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
     int2 *pairs = A.get<int2>(so.entries);
     truss_e = A.get<int32_t>(g.m);
     if (!pairs || !truss_e) return TRUSS_ENOMEM;
-    TR_TRY(tr::run_lists(A, g, scfg, so, pairs, s));
+    // peel variant 4: the barrier-free peel, which needs a triangle id per
+    // list entry (record indices, so records and fewer than 2^32 of them)
+    uint32_t *tids = nullptr;
+    if (ctx->opts.peel_variant == 4 && so.tb && so.records < ((int64_t)1 << 32))
+      tids = A.get<uint32_t>(so.entries);
+    TR_TRY(tr::run_lists(A, g, scfg, so, pairs, tids, s));
     sg.mark();  // 3
     tr::PeelCfg pcfg;
     pcfg.sms = ctx->sms;
     pcfg.variant = ctx->opts.peel_variant;
     if (ctx->opts.wait_limit_ns > 0) pcfg.wait_ns = ctx->opts.wait_limit_ns;
-    int rc = tr::run_peel(A, g, so, pairs, pcfg, truss_e, &pr, s);
+    int rc = tids ? tr::run_peel_async(A, g, so, pairs, tids, so.records, pcfg, truss_e, &pr, s)
+                  : tr::run_peel(A, g, so, pairs, pcfg, truss_e, &pr, s);
     if (rc != TRUSS_OK) return rc;
     sg.mark();  // 4
     st.kmax = pr.kmax;
@@ -416,7 +422,7 @@ int decompose_device_rows(truss_ctx *ctx, tr::Arena &A, const tr::RowsIn &in, in
   int2 *pairs = A.get<int2>(so.entries);
   int32_t *truss_e = A.get<int32_t>(g.m);
   if (!pairs || !truss_e) return TRUSS_ENOMEM;
-  TR_TRY(tr::run_lists(A, g, cfg, so, pairs, s));
+  TR_TRY(tr::run_lists(A, g, cfg, so, pairs, nullptr, s));
   tr::PeelCfg pcfg;
   pcfg.sms = ctx->sms;
   pcfg.variant = ctx->opts.peel_variant;

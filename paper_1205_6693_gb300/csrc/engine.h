@@ -98,6 +98,7 @@ struct SupportOut {
   int64_t entries = 0;       // sum sup = 3 * triangles
   // optional triangle records of the support walk (see support.cu)
   int64_t *tbpre = nullptr;  // [m+1] record-region offsets
+  int64_t records = 0;       // size of the record regions (record indices are below it)
   int2 *tb = nullptr;        // (e_uw, e_vw) records per walked edge e_uv
   int32_t *cuv = nullptr;    // [m] records per edge
 };
@@ -115,8 +116,10 @@ struct SupportCfg {
 int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, cudaStream_t s);
 // Triangle lists: pairs[toff[e] .. toff[e]+sup[e]) = the other two edge ids
 // of each triangle of e (support.cu).
+// tids (nullable, only with records): the record index of each entry's
+// triangle, for the barrier-free peel.
 int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &so, int2 *pairs,
-              cudaStream_t s);
+              uint32_t *tids, cudaStream_t s);
 
 // ---------------------------------------------------------------- peel ---
 struct PeelCfg {
@@ -135,6 +138,11 @@ struct PeelResult {
   unsigned long long entries = 0, decrements = 0, scanned = 0;
 };
 
+// Barrier-free peel (peel_async.cu): needs the list entries' triangle ids
+// (record indices below ntri).
+int run_peel_async(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs,
+                   const uint32_t *tids, int64_t ntri, const PeelCfg &cfg, int32_t *truss,
+                   PeelResult *out, cudaStream_t s);
 int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, const PeelCfg &cfg,
              int32_t *truss, PeelResult *res, cudaStream_t s);
 

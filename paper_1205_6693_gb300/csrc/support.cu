@@ -555,8 +555,8 @@ constexpr int kListU = 4;
 
 __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2 *tb,
                                      const int32_t *cuv, const int64_t *toff,
-                                     unsigned long long *cur, int2 *pairs, int64_t entries,
-                                     int *err) {
+                                     unsigned long long *cur, int2 *pairs, uint32_t *tids,
+                                     int64_t entries, int *err) {
   const int lane = lane_id();
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -570,6 +570,7 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
       int2 rec[kListU];
       int64_t x1[kListU], x2[kListU];
       int eo[kListU];
+      uint32_t ri[kListU];  // record index = triangle id
 #pragma unroll
       for (int k = 0; k < kListU; k++) {
         const int t = t0 + k * 32 + lane;
@@ -579,6 +580,7 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
         const int j = t - (oP - oc);
         eo[k] = (int)(base + o);
         x1[k] = ol + j;
+        ri[k] = (uint32_t)(orr + j);
         rec[k] = t < total ? __ldg(&tb[orr + j]) : make_int2(-1, -1);  // (e_uw, e_vw) on e_uv
       }
 #pragma unroll
@@ -590,6 +592,10 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
         if (x1[k] < entries && x2[k] < entries) {
           pairs[x1[k]] = rec[k];
           pairs[x2[k]] = make_int2(eo[k], rec[k].y);
+          if (tids) {
+            tids[x1[k]] = ri[k];
+            tids[x2[k]] = ri[k];
+          }
         } else {
           atomicExch(err, TRUSS_ECHECK);
         }
@@ -601,7 +607,7 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
 // inedge[0 .. m) = the oriented edges sorted by head v (pass 2's order).
 __global__ void k_lists_vw(int64_t m, const int32_t *inedge, const int64_t *tbpre,
                            const int2 *tb, const int32_t *cuv, unsigned long long *cur,
-                           int2 *pairs, int64_t entries, int *err) {
+                           int2 *pairs, uint32_t *tids, int64_t entries, int *err) {
   const int lane = lane_id();
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -616,6 +622,7 @@ __global__ void k_lists_vw(int64_t m, const int32_t *inedge, const int64_t *tbpr
       int2 rec[kListU];
       int64_t x3[kListU];
       int eo[kListU];
+      uint32_t ri[kListU];
 #pragma unroll
       for (int k = 0; k < kListU; k++) {
         const int t = t0 + k * 32 + lane;
@@ -624,6 +631,7 @@ __global__ void k_lists_vw(int64_t m, const int32_t *inedge, const int64_t *tbpr
         const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
         eo[k] = __shfl_sync(TR_FULL, e, o);
         const int j = t - (oP - oc);
+        ri[k] = (uint32_t)(orr + j);
         rec[k] = t < total ? __ldg(&tb[orr + j]) : make_int2(-1, -1);
       }
 #pragma unroll
@@ -632,8 +640,12 @@ __global__ void k_lists_vw(int64_t m, const int32_t *inedge, const int64_t *tbpr
 #pragma unroll
       for (int k = 0; k < kListU; k++) {
         if (rec[k].y < 0) continue;
-        if (x3[k] < entries) pairs[x3[k]] = make_int2(eo[k], rec[k].x);
-        else atomicExch(err, TRUSS_ECHECK);
+        if (x3[k] < entries) {
+          pairs[x3[k]] = make_int2(eo[k], rec[k].x);
+          if (tids) tids[x3[k]] = ri[k];
+        } else {
+          atomicExch(err, TRUSS_ECHECK);
+        }
       }
     }
   }
@@ -832,13 +844,14 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
   out->inedge = inedge;
   out->inoff = inoff;
   out->tbpre = recs ? tbpre : nullptr;
+  out->records = recs ? R : 0;
   out->tb = recs;
   out->cuv = recs ? cuv : nullptr;
   return TRUSS_OK;
 }
 
 int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &so, int2 *pairs,
-              cudaStream_t s) {
+              uint32_t *tids, cudaStream_t s) {
   const int64_t m = g.m;
   if (m == 0 || so.entries == 0) return TRUSS_OK;
   if (so.tb) {
@@ -854,9 +867,9 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
     TR_CUDA(cudaGetDevice(&dev));
     if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     k_lists_from_records<<<sms * 8, 256, 0, s>>>(m, so.tbpre, so.tb, so.cuv, so.toff, cur, pairs,
-                                                 so.entries, err);
+                                                 tids, so.entries, err);
     TR_LAUNCHED();
-    k_lists_vw<<<sms * 8, 256, 0, s>>>(m, inedge, so.tbpre, so.tb, so.cuv, cur, pairs,
+    k_lists_vw<<<sms * 8, 256, 0, s>>>(m, inedge, so.tbpre, so.tb, so.cuv, cur, pairs, tids,
                                        so.entries, err);
     TR_LAUNCHED();
     int h_err = 0;

@@ -287,3 +287,69 @@ def test_lists_by_second_walk():
             assert_same(c, n, src, dst)
     finally:
         c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_async():
+    from paper_1205_6693_gb300 import truss as T
+    c = T.Context(0, peel_variant=4)
+    yield c
+    c.close()
+
+
+def _async_cases():
+    yield "tiny", graphgen.tiny()
+    for sc, seed in ((10, 2), (13, 4), (15, 6)):
+        s, d = graphgen.rmat_raw(sc, 16 << sc, seed=seed)
+        yield f"rmat{sc}", (1 << sc, s, d)
+    n = 4000
+    s, d = graphgen.er(n, 16000, seed=21)
+    perm = graphgen.permutation(n, seed=21, stream=1)
+    s, d = graphgen.add_cliques(s, d, perm[:100], [6, 11, 17, 23, 40])
+    yield "er+cliques", (n, s, d)
+
+
+ASYNC_CASES = list(_async_cases())
+
+
+@pytest.mark.parametrize("name,case", ASYNC_CASES, ids=[c[0] for c in ASYNC_CASES])
+def test_barrier_free_peel(ctx_async, name, case):
+    """Peel variant 4 (triangle destroyed-bits, work queue per level) against
+    the oracle, bit-exact."""
+    n, src, dst = case
+    assert_same(ctx_async, n, src, dst)
+
+
+def test_barrier_free_peel_fig2_and_cliques(ctx_async):
+    from test_oracle import fig2
+    classes = fig2()
+    edges = sorted(classes)
+    src = np.array([a for a, _ in edges], np.int32)
+    dst = np.array([b for _, b in edges], np.int32)
+    _, tr, kmax = gpu_run(ctx_async, 12, src, dst)
+    assert [int(t) for t in tr] == [classes[e] for e in edges] and kmax == 5
+    for n in (3, 9, 40):
+        a, b = np.triu_indices(n, 1)
+        _, tr, kmax = gpu_run(ctx_async, n, a.astype(np.int32), b.astype(np.int32))
+        assert (tr == n).all() and kmax == n
+
+
+def test_barrier_free_peel_mid_full_size(ctx_async):
+    _check_full(ctx_async, "mid", graphgen.mid)
+
+
+def test_barrier_free_peel_bounded_wait():
+    from paper_1205_6693_gb300 import truss as T
+    n, (src, dst) = 2 ** 12, graphgen.rmat_raw(12, 16 * 2 ** 12, seed=9)
+    c = T.Context(0, wait_limit_ns=1, peel_variant=4)
+    try:
+        with pytest.raises(T.TrussError) as ei:
+            gpu_run(c, n, src, dst)
+        assert ei.value.code == T.TRUSS_ETIMEOUT
+    finally:
+        c.close()
+    c2 = T.Context(0, peel_variant=4)
+    try:
+        assert_same(c2, n, src, dst)
+    finally:
+        c2.close()
