@@ -1,35 +1,22 @@
 // Edge support (Definition 1; Algorithm 2 step 2) and per-edge triangle lists.
 //
-// Triangles are listed once each, from their lowest-ranked vertex u in the
-// (degree, id) order (the in-memory triangle listing the paper cites for step
-// 2, with the out-list bound of Theorem 1): for v in out(u), every w in
-// out(v) that is also in out(u) closes the triangle (u, v, w), whose edges
-// are e_uv, e_uw (both in u's out-list) and e_vw (in v's out-list).
+// Vertices are ranked by (degree, id) and every edge points from its
+// lower-ranked end u to its higher-ranked end v (the degree order of
+// Theorem 1).  A triangle u < v < w is found once, from its middle vertex v
+// (k_support_v, below): w lies in out(v) and in out(u) after v.  Its edges
+// are e_uv, e_uw (both in out(u)) and e_vw (in out(v)).  Counts: supA[e] =
+// triangles in which e is e_uv or e_uw, supB[e] = triangles in which it is
+// e_vw; sup = supA + supB.
 //
-// Work is split evenly: the walk of edge (u, v) costs |out(v)|, so the
-// oriented edges are cut into ranges of equal total cost (prefix sum plus a
-// binary search per range) and warps take ranges round-robin.  For each
-// vertex u its range touches, the warp stages out(u) in shared memory (if it
-// fits; otherwise it reads it from global memory).  For each v in its part
-// of out(u) it intersects out(v) with the part of out(u) after v by a warp
-// merge path: out(v) is staged in shared memory in chunks, the window of
-// out(u) is cut to the chunk's value range, and the merged sequence of the
-// two sorted lists is split evenly over the 32 lanes (one binary search per
-// lane on its diagonal, then a branch-free merge), so each list element costs
-// about one step instead of a search.
-//
-// Counts are split by who can see them: supA[e] (e in out(u)) collects the
-// triangles found while u is processed -- in shared memory, then stored once
-// (or added, when u's out-list is shared by several ranges) -- and supB[e]
-// collects, by global atomics, the triangles in which e is the (v, w) edge.
-// sup = supA + supB.
-//
-// The second pass (MODE 1) repeats the walk and writes, for every triangle,
-// one entry (the other two edge ids) into each of its three edges' lists:
-// list(e) = pairs[toff[e] .. toff[e] + sup[e]), the first supA[e] entries
-// from the walk of e's tail (shared-memory cursors when one warp walks all of
-// the tail's out-list, else global cursors curA), the rest from global
-// cursors curB.
+// The walk also records each triangle as (e_uw, e_vw) in a region of e_uv
+// (the triangle records), from which two streaming passes build the dense
+// per-edge lists list(e) = pairs[toff[e] .. toff[e] + sup[e]).  When the
+// records do not fit in device memory, a second, owner-by-owner walk
+// (k_list_walk) writes the lists directly: for v in out(u) it intersects
+// out(v) with the part of out(u) after v by a warp merge path (out(v) staged
+// in chunks, the window of out(u) cut to the chunk's value range, the merged
+// sequence split evenly over the 32 lanes), and writes one entry into each of
+// the triangle's three lists.
 #include <climits>
 
 #include "engine.h"
@@ -41,45 +28,33 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int64_t kRangeWork = 16384;  // target walk cost per range
 constexpr int kEdgeCost = 64;          // fixed walk cost per oriented edge (entries)
-// Out-list entries staged per warp: counting pass (int32 counters) and list
-// pass (int64 cursors).
-template <int MODE>
-struct Cap {
-  static constexpr int value = MODE == 0 ? 512 : 256;
-};
-constexpr int kAChunk = 512;     // out(v) entries staged per warp per chunk (merge path)
-constexpr int kHashSlots = 2048; // per-warp position table of a staged out(u) (MODE 0)
-template <int MODE>
-__host__ __device__ constexpr size_t warp_smem() {
-  // counters (int32) or cursors (int64), L (int32), then MODE 0: the
-  // position table (uint16), which the merge path of unstaged owners reuses
-  // as its out(v) chunk; MODE 1: the out(v) chunk (int32)
-  return (size_t)Cap<MODE>::value * ((MODE == 0 ? 4 : 8) + 4) +
-         (MODE == 0 ? (size_t)kHashSlots * 2 : (size_t)kAChunk * 4);
-}
-static_assert(kHashSlots * 2 >= kAChunk * 4, "chunk buffer aliases the position table");
+// Head walk (support): out(v) of up to kHeadCap entries staged per warp with
+// its counts (int32) and a position table of kHashSlots uint16 slots.
+constexpr int kHeadCap = 512;
+constexpr int kHashSlots = 2048;
+constexpr size_t kHeadSmem = (size_t)kHeadCap * 8 + (size_t)kHashSlots * 2;
+// List walk (the list builder used when the triangle records do not fit):
+// out(u) of up to kListCap entries staged with its cursors (int64), and out(v)
+// staged kAChunk entries at a time.
+constexpr int kListCap = 256;
+constexpr int kAChunk = 512;
+constexpr size_t kListSmem = (size_t)kListCap * 12 + (size_t)kAChunk * 4;
 
-struct SupArgs {
+// Arguments of the list walk (owner by owner, lists written directly).
+struct ListArgs {
   int64_t n, m;
   const int64_t *offp;
   const int32_t *adjp;
   const int32_t *esrc;
-  const int64_t *wpre;  // [m+1] exclusive prefix of the walk cost per edge
+  const int64_t *wpre;  // [m+1] exclusive prefix of the owner-centric walk cost
   int64_t W;            // total walk cost
   int64_t P;            // number of ranges
   int stage_max;        // stage out(u) in shared memory when |out(u)| <= this
-  int32_t *supA;        // MODE 0: owner counts; MODE 1: read
-  int32_t *supB;        // MODE 0: (v, w)-edge counts
-  unsigned long long *curA;  // MODE 1: next slot of e's owner part (starts at toff[e])
-  unsigned long long *curB;  // MODE 1: next slot of e's other part (toff[e] + supA[e])
-  int2 *pairs;          // MODE 1
-  int64_t entries;      // MODE 1: size of pairs (writes beyond it are dropped)
-  int *err;             // MODE 1: set to TRUSS_ECHECK if a list would overflow
-  // MODE 0, optional: per walked edge e = (u, v), the triangles (u, v, w) it
-  // closes, as (e_uw, e_vw) records in tb[tbpre[e] .. tbpre[e] + cuv[e]).
-  const int64_t *tbpre;  // [m+1] exclusive prefix of min(|out(v)|, |out(u) after v|)
-  int2 *tb;
-  int32_t *cuv;
+  unsigned long long *curA;  // next slot of e's owner part (starts at toff[e])
+  unsigned long long *curB;  // next slot of e's other part (toff[e] + supA[e])
+  int2 *pairs;
+  int64_t entries;      // size of pairs (writes beyond it are dropped)
+  int *err;             // set to TRUSS_ECHECK if a list would overflow
 };
 
 // First e in [0, m] with wpre[e] >= x.
@@ -117,37 +92,21 @@ struct OutList {
   }
 };
 
-// Record the triangle (u, v, w) found as out(v)[evw - ob] == L[q] while
-// walking edge (u, L[io]).  C = owner counters (MODE 0, int32) or owner
-// cursors (MODE 1, int64).
-template <int MODE>
-__device__ __forceinline__ void found(const SupArgs &a, int64_t bu, void *Cv, int io, int q,
-                                      int64_t evw, int *uvc) {
-  if (MODE == 0) {
-    int32_t *C = (int32_t *)Cv;
-    atomicAdd(&a.supB[evw], 1);
-    atomicAdd(&C[q], 1);
-    if (a.tb) {
-      // record the triangle under e_uv; C[io] gets the pair's total later
-      const int64_t euv = bu + io;
-      const int r = atomicAdd(uvc, 1);
-      a.tb[__ldg(&a.tbpre[euv]) + r] = make_int2((int)(bu + q), (int)evw);
-    } else {
-      atomicAdd(&C[io], 1);
-    }
+// Write the triangle (u, v, w), found as out(v)[evw - ob] == L[q] while
+// walking edge (u, L[io]), into its three lists.  C = the owner cursors of
+// out(u) (shared or global).
+__device__ __forceinline__ void found(const ListArgs &a, int64_t bu, unsigned long long *C,
+                                      int io, int q, int64_t evw) {
+  const int64_t euv = bu + io, euw = bu + q;
+  const int64_t x1 = (int64_t)atomicAdd(&C[io], 1ull);
+  const int64_t x2 = (int64_t)atomicAdd(&C[q], 1ull);
+  const int64_t x3 = (int64_t)atomicAdd(&a.curB[evw], 1ull);
+  if (x1 < a.entries && x2 < a.entries && x3 < a.entries) {
+    a.pairs[x1] = make_int2((int)euw, (int)evw);
+    a.pairs[x2] = make_int2((int)euv, (int)evw);
+    a.pairs[x3] = make_int2((int)euv, (int)euw);
   } else {
-    unsigned long long *C = (unsigned long long *)Cv;
-    const int64_t euv = bu + io, euw = bu + q;
-    const int64_t x1 = (int64_t)atomicAdd(&C[io], 1ull);
-    const int64_t x2 = (int64_t)atomicAdd(&C[q], 1ull);
-    const int64_t x3 = (int64_t)atomicAdd(&a.curB[evw], 1ull);
-    if (x1 < a.entries && x2 < a.entries && x3 < a.entries) {
-      a.pairs[x1] = make_int2((int)euw, (int)evw);
-      a.pairs[x2] = make_int2((int)euv, (int)evw);
-      a.pairs[x3] = make_int2((int)euv, (int)euw);
-    } else {
-      atomicExch(a.err, TRUSS_ECHECK);
-    }
+    atomicExch(a.err, TRUSS_ECHECK);
   }
 }
 
@@ -159,9 +118,9 @@ __device__ __forceinline__ void found(const SupArgs &a, int64_t bu, void *Cv, in
 // merged order (A first on ties), finds its start by a binary search on its
 // diagonal and then merges K steps; an A entry equal to the current B head
 // is a triangle.
-template <int MODE, bool STAGED>
-__device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList<STAGED> &ol,
-                                     void *Cv, int i0, int i1, int32_t *Abuf, int *uvc) {
+template <bool STAGED>
+__device__ __forceinline__ void walk(const ListArgs &a, int64_t bu, const OutList<STAGED> &ol,
+                                     unsigned long long *C, int i0, int i1, int32_t *Abuf) {
   const int lane = lane_id();
   const int d = ol.d;
   const int Lmax = ol.at(d - 1);
@@ -203,7 +162,7 @@ __device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList
           int bv = jb < bc ? ol.at(blo + jb) : INT_MAX;
           for (; p < pend; p++) {
             const bool takeA = av <= bv;
-            if (takeA && av == bv) found<MODE>(a, bu, Cv, io, blo + jb, ob + cA + ia, uvc);
+            if (takeA && av == bv) found(a, bu, C, io, blo + jb, ob + cA + ia);
             ia += takeA;
             jb += !takeA;
             av = ia < ac ? Abuf[ia] : INT_MAX;
@@ -211,17 +170,6 @@ __device__ __forceinline__ void walk(const SupArgs &a, int64_t bu, const OutList
           }
         }
         blo = bhi;
-      }
-      if (MODE == 0 && a.tb) {
-        // close the pair (u, v): its record count, and its owner count C[io]
-        __syncwarp();
-        if (lane == 0) {
-          const int tot = *uvc;
-          a.cuv[bu + io] = tot;
-          if (tot) atomicAdd(&((int32_t *)Cv)[io], tot);
-          *uvc = 0;
-        }
-        __syncwarp();
       }
     }
   }
@@ -258,7 +206,9 @@ struct SupVArgs {
   int64_t W, P;
   int stage_max;
   int32_t *supA, *supB;
-  const int64_t *tbpre;  // optional records, as SupArgs
+  // optional: per edge e = (u, v), the triangles (u, v, w) it closes, as
+  // (e_uw, e_vw) records in tb[tbpre[e] .. tbpre[e] + cuv[e])
+  const int64_t *tbpre;  // [m+1] exclusive prefix of min(|out(v)|, |out(u) after v|)
   int2 *tb;
   int32_t *cuv;
 };
@@ -346,11 +296,10 @@ __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t
 __global__ void __launch_bounds__(kBlock, 3) k_support_v(SupVArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  unsigned char *base = smem_raw + (size_t)warp * warp_smem<0>();
-  constexpr int CAP = Cap<0>::value;
+  unsigned char *base = smem_raw + (size_t)warp * kHeadSmem;
   int32_t *Cs = (int32_t *)base;
-  int32_t *Ls = Cs + CAP;
-  unsigned short *Hs = (unsigned short *)(Ls + CAP);
+  int32_t *Ls = Cs + kHeadCap;
+  unsigned short *Hs = (unsigned short *)(Ls + kHeadCap);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = gw; r < a.P; r += nw) {
@@ -440,21 +389,18 @@ __global__ void k_walk_cost_v(int64_t m, const int64_t *offp, const int32_t *adj
   }
 }
 
-// Warps take equal-cost ranges of oriented edges round-robin.
-template <int MODE>
-__global__ void __launch_bounds__(kBlock, MODE == 0 ? 3 : 4) k_support(SupArgs a) {
-  constexpr int CAP = Cap<MODE>::value;
+// The list walk: warps take equal-cost ranges of oriented edges round-robin.
+// list(e)'s first supA[e] entries come from the walk of e's tail (cursors in
+// shared memory when one warp walks all of the tail's out-list, else the
+// global cursors curA), the rest from the global cursors curB.
+__global__ void __launch_bounds__(kBlock, 4) k_list_walk(ListArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  unsigned char *base = smem_raw + (size_t)warp * warp_smem<MODE>();
-  // layout: counters/cursors (8-byte aligned first), then L, then the out(v) chunk
-  void *Cs = base;
-  int32_t *Ls = (int32_t *)(base + (size_t)CAP * (MODE == 0 ? 4 : 8));
-  int32_t *Abuf = Ls + CAP;  // out(v) chunk of the merge path
-  __shared__ int s_uvc[kBlock / 32];
-  int *uvc = &s_uvc[warp];
-  if (lane == 0) *uvc = 0;
-  __syncwarp();
+  unsigned char *base = smem_raw + (size_t)warp * kListSmem;
+  // layout: cursors (8-byte aligned first), then L, then the out(v) chunk
+  unsigned long long *Cs = (unsigned long long *)base;
+  int32_t *Ls = (int32_t *)(base + (size_t)kListCap * 8);
+  int32_t *Abuf = Ls + kListCap;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = gw; r < a.P; r += nw) {
@@ -471,31 +417,17 @@ __global__ void __launch_bounds__(kBlock, MODE == 0 ? 3 : 4) k_support(SupArgs a
       const int i1 = min(iend, d - 1);  // the last out-neighbour closes no triangle here
       if (i0 >= i1) continue;
       const bool whole = i0 == 0 && iend >= d - 1;  // this warp walks all of out(u)
-      const bool staged = d <= a.stage_max;
-      void *C;
-      if (staged) {
+      if (d <= a.stage_max) {
         for (int q = lane; q < d; q += 32) {
           Ls[q] = __ldg(&a.adjp[bu + q]);
-          if (MODE == 0) ((int32_t *)Cs)[q] = 0;
-          else ((unsigned long long *)Cs)[q] = (unsigned long long)__ldg(&a.curA[bu + q]);
+          Cs[q] = (unsigned long long)__ldg(&a.curA[bu + q]);
         }
         __syncwarp();
-        C = Cs;
-        if (MODE == 1 && !whole) C = a.curA + bu;  // cursors shared by several ranges
         OutList<true> ol{Ls, d};
-        walk<MODE, true>(a, bu, ol, C, i0, i1, Abuf, uvc);
+        walk<true>(a, bu, ol, whole ? Cs : a.curA + bu, i0, i1, Abuf);
       } else {
-        C = MODE == 0 ? (void *)(a.supA + bu) : (void *)(a.curA + bu);
         OutList<false> ol{a.adjp + bu, d};
-        walk<MODE, false>(a, bu, ol, C, i0, i1, Abuf, uvc);
-      }
-      __syncwarp();
-      if (MODE == 0 && staged) {
-        const int32_t *Ci = (const int32_t *)Cs;
-        for (int q = lane; q < d; q += 32) {
-          if (whole) a.supA[bu + q] = Ci[q];
-          else if (Ci[q] != 0) atomicAdd(&a.supA[bu + q], Ci[q]);
-        }
+        walk<false>(a, bu, ol, a.curA + bu, i0, i1, Abuf);
       }
       __syncwarp();
     }
@@ -690,19 +622,18 @@ __global__ void k_cursors(int64_t m, const int64_t *toff, const int32_t *supA,
   }
 }
 
-// The owner-centric list walk (k_support<1>), used when the triangle
-// records do not fit.
-int launch_list_walk(SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
+// The owner-centric list walk, used when the triangle records do not fit.
+int launch_list_walk(ListArgs a, const SupportCfg &cfg, cudaStream_t s) {
   int dev = 0, sms = cfg.sms;
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const size_t smem = (size_t)(kBlock / 32) * warp_smem<1>();
-  // the per-warp buffers (dynamic) plus small static counters exceed the
-  // default 48 KB window: opt in to the larger per-block limit
-  TR_CUDA(cudaFuncSetAttribute(k_support<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = (size_t)(kBlock / 32) * kListSmem;
+  // the per-warp buffers exceed the default 48 KB window: opt in to the
+  // larger per-block limit
+  TR_CUDA(cudaFuncSetAttribute(k_list_walk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   int occ = 0;
-  TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_support<1>, kBlock, smem));
+  TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_list_walk, kBlock, smem));
   if (occ < 1) occ = 1;
   const int grid = sms * occ;
   const int64_t warps = (int64_t)grid * (kBlock / 32);
@@ -710,9 +641,8 @@ int launch_list_walk(SupArgs a, const SupportCfg &cfg, cudaStream_t s) {
   if (P < warps) P = warps;
   if (P > a.m) P = a.m > 0 ? a.m : 1;
   a.P = P;
-  const int cap = Cap<1>::value;
-  a.stage_max = cfg.stage_max > 0 && cfg.stage_max < cap ? cfg.stage_max : cap;
-  k_support<1><<<grid, kBlock, smem, s>>>(a);
+  a.stage_max = cfg.stage_max > 0 && cfg.stage_max < kListCap ? cfg.stage_max : kListCap;
+  k_list_walk<<<grid, kBlock, smem, s>>>(a);
   TR_LAUNCHED();
   return TRUSS_OK;
 }
@@ -721,7 +651,7 @@ int launch_walk_v(SupVArgs a, const SupportCfg &cfg, cudaStream_t s) {
   int dev = 0, sms = cfg.sms;
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const size_t smem = (size_t)(kBlock / 32) * warp_smem<0>();
+  const size_t smem = (size_t)(kBlock / 32) * kHeadSmem;
   TR_CUDA(cudaFuncSetAttribute(k_support_v, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   int occ = 0;
@@ -733,8 +663,7 @@ int launch_walk_v(SupVArgs a, const SupportCfg &cfg, cudaStream_t s) {
   if (P < warps) P = warps;
   if (P > a.m) P = a.m > 0 ? a.m : 1;
   a.P = P;
-  const int cap = Cap<0>::value;
-  a.stage_max = cfg.stage_max > 0 && cfg.stage_max < cap ? cfg.stage_max : cap;
+  a.stage_max = cfg.stage_max > 0 && cfg.stage_max < kHeadCap ? cfg.stage_max : kHeadCap;
   k_support_v<<<grid, kBlock, smem, s>>>(a);
   TR_LAUNCHED();
   return TRUSS_OK;
@@ -899,7 +828,7 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
   TR_CUDA(cudaStreamSynchronize(s));
   k_cursors<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.supA, curA, curB);
   TR_LAUNCHED();
-  SupArgs a{};
+  ListArgs a{};
   a.n = g.n;
   a.m = m;
   a.offp = g.offp;
@@ -907,7 +836,6 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
   a.esrc = g.esrc;
   a.wpre = wpre;
   a.W = W;
-  a.supA = so.supA;
   a.curA = curA;
   a.curB = curB;
   a.pairs = pairs;
@@ -942,6 +870,25 @@ __global__ void k_count_walk(int64_t n, const int64_t *offp, unsigned long long 
   for (int o = 16; o >= 1; o >>= 1) local += __shfl_down_sync(TR_FULL, local, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(acc, local);
 }
+// Algorithmic bytes of the owner-centric list walk: per owner u of
+// out-degree d >= 2, its offsets, out(u) and its cursors (16 + 8d); per
+// walked edge (u, v), v's offsets and out(v) (16 + 4 |out(v)|).
+__global__ void k_count_list_walk(int64_t n, const int64_t *offp, const int32_t *adjp,
+                                  unsigned long long *acc) {
+  unsigned long long local = 0;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bu = offp[u], d = offp[u + 1] - bu;
+    if (d < 2) continue;
+    local += 16ull + 8ull * (unsigned long long)d;
+    for (int64_t i = 0; i < d - 1; i++) {
+      const int v = adjp[bu + i];
+      local += 16ull + 4ull * (unsigned long long)(offp[v + 1] - offp[v]);
+    }
+  }
+  for (int o = 16; o >= 1; o >>= 1) local += __shfl_down_sync(TR_FULL, local, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(acc, local);
+}
 }  // namespace
 
 // Algorithmic bytes of the support pass: walk bytes + per triangle the
@@ -956,16 +903,23 @@ int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records,
     k_count_walk<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, g.offp, acc);
     TR_LAUNCHED();
   }
-  unsigned long long h = 0;
+  unsigned long long h = 0, hl = 0;
   TR_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
   TR_CUDA(cudaStreamSynchronize(s));
+  if (!records && g.n > 0 && g.m > 0) {
+    TR_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
+    k_count_list_walk<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, g.offp, g.adjp, acc);
+    TR_LAUNCHED();
+    TR_CUDA(cudaMemcpyAsync(&hl, acc, sizeof(hl), cudaMemcpyDeviceToHost, s));
+    TR_CUDA(cudaStreamSynchronize(s));
+  }
   // lists from records: the record read by both passes, three entries, two
   // cursor RMWs (56 B), and per edge the cursor set-up and both passes'
   // offset/count reads (56 B; the head-order sort is not counted); lists by
   // a second walk: the walk again plus 60 B per triangle
   *b_sup = (double)h + (records ? 16.0 : 8.0) * (double)triangles;
   *b_lists = records ? 56.0 * (double)triangles + 56.0 * (double)g.m
-                     : (double)h + 60.0 * (double)triangles;
+                     : (double)hl + 60.0 * (double)triangles;
   return TRUSS_OK;
 }
 
