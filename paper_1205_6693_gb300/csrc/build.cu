@@ -152,8 +152,16 @@ int build_csr(Arena &A, const RowsIn &in, Csr *out, int32_t *d_err, cudaStream_t
   out->offp = offp;
 
   if (rows == 0) {
+    // no edges: empty out-lists, and every vertex keeps its id as its rank
+    int32_t *order = A.get<int32_t>(n);
+    if (!order) return TRUSS_ENOMEM;
     TR_CUDA(cudaMemsetAsync(offp, 0, sizeof(int64_t) * (n + 1), s));
+    if (n > 0) {
+      k_iota<<<grid_for(n, kBlock, maxg), kBlock, 0, s>>>(n, order);
+      TR_LAUNCHED();
+    }
     out->m = 0;
+    out->order = order;
     out->adjp = A.get<int32_t>(1);
     out->esrc = A.get<int32_t>(1);
     return TRUSS_OK;

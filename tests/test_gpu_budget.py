@@ -73,3 +73,15 @@ def test_budget_edge_cases(ctx):
     assert list(tr) == [2, 2, 2, 2, -1] and list(sup) == [0, 0, 0, 0, -1] and k == 2
     with pytest.raises(T.TrussError):
         gpu_budget(ctx, 5, src, dst, 0)
+
+
+def test_budget_with_host_buffers_and_duplicates(ctx):
+    n, src, dst = graphgen.tiny()
+    src = np.concatenate([src, dst[:500], np.arange(20, dtype=np.int32)])
+    dst = np.concatenate([dst, src[:500], np.arange(20, dtype=np.int32)])
+    sup = np.empty(len(src), np.int32)
+    tr = np.empty(len(src), np.int32)
+    k = ctx.decompose_budget(n, src, dst, 5000, sup, tr)
+    ref = oracle.truss(n, src, dst)
+    assert np.array_equal(sup, ref.support) and np.array_equal(tr, ref.truss)
+    assert k == ref.kmax

@@ -94,3 +94,15 @@ def test_truss_inside_core_on_gpu(ctx):
     tr = tr.cpu().numpy()
     ok = tr > 0
     assert (tr[ok] <= np.minimum(core[s[ok]], core[d[ok]]) + 1).all()
+
+
+def test_core_empty_and_invalid(ctx):
+    from paper_1205_6693_gb300 import truss as T
+    e = np.zeros(0, np.int32)
+    out = np.full(6, -7, np.int32)
+    assert ctx.core(6, e, e, out) == 0
+    assert (out == 0).all()  # every vertex without edges has core number 0
+    with pytest.raises(T.TrussError) as ei:
+        ctx.core(3, np.array([0, 5], np.int32), np.array([1, 2], np.int32),
+                 np.empty(3, np.int32))
+    assert ei.value.code == T.TRUSS_EINVAL

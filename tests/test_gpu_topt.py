@@ -164,3 +164,27 @@ def test_top_mid_against_stored_oracle(ctx):
     assert got == want_cls
     st = ctx.stats()
     assert st["candidates"] < st["m"] // 4  # the candidate subgraph is a small part
+
+
+def test_upper_bound_and_top_with_host_buffers(ctx):
+    """Host (numpy) inputs and outputs go through the same entry points."""
+    n, src, dst = graphgen.tiny()
+    sup = np.empty(len(src), np.int32)
+    ps = np.empty(len(src), np.int32)
+    ctx.upper_bound(n, src, dst, sup, ps)
+    osup, ops = oracle.psi(n, src, dst)
+    assert np.array_equal(sup, osup) and np.array_equal(ps, ops)
+    out = np.empty(len(src), np.int32)
+    k = ctx.top(n, src, dst, 4, out)
+    want, wk = oracle.top(n, src, dst, 4)
+    assert k == wk and np.array_equal(out, want)
+
+
+def test_top_rejects_bad_ids(ctx):
+    from paper_1205_6693_gb300 import truss as T
+    src = np.array([0, 1, 7], np.int32)
+    dst = np.array([1, 2, 0], np.int32)
+    out = np.empty(3, np.int32)
+    with pytest.raises(T.TrussError) as ei:
+        ctx.top(5, src, dst, 1, out)
+    assert ei.value.code == T.TRUSS_EINVAL
