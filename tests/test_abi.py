@@ -100,3 +100,32 @@ def test_chung_lu_sorted_selection_equals_hash_set_selection():
         a = graphgen.chung_lu(n, m, 20.0, cap, 2.1, seed=seed)
         b = graphgen.chung_lu(n, m, 20.0, cap, 2.1, seed=seed, sorted_dedup=True)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/truss.h compiles as C99 with warnings as errors, and a C client
+    links against the library (no GPU needed: truss_ctx_create reports the
+    missing device as an error code)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    from paper_1205_6693_gb300 import truss as T
+    lib = T.load()._name
+    src = tmp_path / "client.c"
+    src.write_text(
+        '#include "truss.h"\n#include <stdio.h>\n'
+        "int main(void) {\n"
+        "  truss_ctx *ctx = 0;\n"
+        "  int rc = truss_ctx_create(&ctx, 0, 0);\n"
+        '  printf("%d %s\\n", rc, truss_strerror(rc));\n'
+        "  if (ctx) truss_ctx_destroy(ctx);\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "client"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           lib, "-Wl,-rpath," + os.path.dirname(lib)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0
+    rc = int(out.stdout.split()[0])
+    assert rc in (T.TRUSS_OK, T.TRUSS_ECUDA, T.TRUSS_EINVAL)
