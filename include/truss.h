@@ -95,7 +95,14 @@ typedef struct truss_opts {
    * path taken anyway when the support walk's triangle records do not fit
    * in free device memory (0 = records whenever they fit). */
   int32_t lists_by_walk;
-  int32_t reserved[6];
+  /* Non-zero: whenever the triangle records are used, leave each edge's own
+   * triangles (those it closes as the walked edge) in the records instead of
+   * copying them into its list; the list pass then writes a third less, and
+   * the peel reads each list in two stretches.  0 = whole lists when they fit
+   * in free device memory, own parts in place when only those fit.  Ignored
+   * by peel variant 4, which needs whole lists. */
+  int32_t lists_in_place;
+  int32_t reserved[5];
 } truss_opts;
 
 /* Create a context bound to CUDA device `device` (ordinal).  opts may be NULL
@@ -217,7 +224,10 @@ typedef struct truss_run_stats {
    * candidate subgraphs were decomposed */
   int64_t candidates;
   int32_t rounds;
-  int32_t reserved0;
+  /* how the triangle lists were built: 0 = none (support only), 1 = by a
+   * second walk of the graph, 2 = whole, from the records, 3 = from the
+   * records with each edge's own part left in place */
+  int32_t lists_layout;
   /* peel work (decompositions): triangle-list entries read, residual
    * decrements, alive-list entries scanned */
   int64_t peel_entries, peel_decrements, peel_scanned;

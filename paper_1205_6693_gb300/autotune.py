@@ -1,7 +1,7 @@
 """Schedule autotuner for the truss library.
 
 The schedule fields of ``truss_opts`` (support walk range size, hub staging
-threshold, per-edge range cost, peel kernel variant) change how the work is
+threshold, per-edge range cost, peel kernel variant, list layout) change how the work is
 laid out on the GPU, never what is computed: every schedule returns the same
 supports and truss numbers.  This module picks them per GPU and per input
 size bucket by timing candidates through the C ABI (the library's own CUDA
@@ -36,6 +36,7 @@ SPACE: dict[str, tuple[int, ...]] = {
     "support_stage_max": (0, 64, 128, 256),
     "support_pair_cost": (0, 16, 32, 128, 256),
     "peel_variant": (0, 1, 3, 4),
+    "lists_in_place": (0, 1),
 }
 # Stage-time keys of truss_last_stats each knob is judged on.
 OBJECTIVE: dict[str, tuple[str, ...]] = {
@@ -43,6 +44,7 @@ OBJECTIVE: dict[str, tuple[str, ...]] = {
     "support_stage_max": ("ms_support", "ms_lists"),
     "support_pair_cost": ("ms_support", "ms_lists"),
     "peel_variant": ("ms_lists", "ms_peel"),  # variant 4 also changes the list pass
+    "lists_in_place": ("ms_lists", "ms_peel"),
 }
 
 _lock = threading.Lock()

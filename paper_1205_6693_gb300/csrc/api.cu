@@ -289,6 +289,8 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   tr::SupportCfg scfg;
   scfg.sms = ctx->sms;
   scfg.records = want_truss && !ctx->opts.lists_by_walk;
+  scfg.full_lists = ctx->opts.peel_variant == 4;
+  scfg.in_place = ctx->opts.lists_in_place != 0;
   scfg.pair_cost = ctx->opts.support_pair_cost;
   scfg.range_work = ctx->opts.support_range_work;
   scfg.stage_max = ctx->opts.support_stage_max;
@@ -314,22 +316,26 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   int32_t *truss_e = nullptr;
   tr::PeelResult pr;
   if (want_truss) {
-    int2 *pairs = A.get<int2>(so.entries);
+    // peel variant 4: the barrier-free peel, which needs the full lists and
+    // a triangle id per list entry (record indices, so records and fewer
+    // than 2^32 of them)
+    const bool async = ctx->opts.peel_variant == 4 && so.tb && !so.in_place &&
+                       so.records < ((int64_t)1 << 32);
+    int2 *pairs = A.get<int2>(tr::list_rest_entries(so));
     truss_e = A.get<int32_t>(g.m);
     if (!pairs || !truss_e) return TRUSS_ENOMEM;
-    // peel variant 4: the barrier-free peel, which needs a triangle id per
-    // list entry (record indices, so records and fewer than 2^32 of them)
-    uint32_t *tids = nullptr;
-    if (ctx->opts.peel_variant == 4 && so.tb && so.records < ((int64_t)1 << 32))
-      tids = A.get<uint32_t>(so.entries);
-    TR_TRY(tr::run_lists(A, g, scfg, so, pairs, tids, s));
+    // short of memory for the ids, the full lists go to the level-synchronous peel
+    uint32_t *tids = async ? A.get<uint32_t>(so.entries) : nullptr;
+    tr::TriLists lists;
+    TR_TRY(tr::run_lists(A, g, scfg, so, pairs, tids, &lists, s));
+    st.lists_layout = !so.tb ? 1 : so.in_place ? 3 : 2;
     sg.mark();  // 3
     tr::PeelCfg pcfg;
     pcfg.sms = ctx->sms;
     pcfg.variant = ctx->opts.peel_variant;
     if (ctx->opts.wait_limit_ns > 0) pcfg.wait_ns = ctx->opts.wait_limit_ns;
     int rc = tids ? tr::run_peel_async(A, g, so, pairs, tids, so.records, pcfg, truss_e, &pr, s)
-                  : tr::run_peel(A, g, so, pairs, pcfg, truss_e, &pr, s);
+                  : tr::run_peel(A, g, so, lists, pcfg, truss_e, &pr, s);
     if (rc != TRUSS_OK) return rc;
     sg.mark();  // 4
     st.kmax = pr.kmax;
@@ -380,11 +386,12 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   st.launches = tr::take_launches();
   if (ctx->opts.count_bytes) {
     double bs = 0, bl = 0;
-    TR_TRY(tr::count_support_bytes(A, g, st.triangles, so.tb != nullptr, &bs, &bl, s));
+    TR_TRY(tr::count_support_bytes(A, g, st.triangles, so.tb != nullptr, so.in_place, &bs, &bl,
+                                   s));
     st.bytes_support = bs;
     st.bytes_lists = want_truss ? bl : 0.0;
     if (want_truss)
-      st.bytes_peel = 28.0 * (double)g.m + 16.0 * (double)pr.entries +
+      st.bytes_peel = (so.in_place ? 40.0 : 28.0) * (double)g.m + 16.0 * (double)pr.entries +
                       8.0 * (double)pr.decrements + 16.0 * (double)pr.scanned;
   }
   ctx->last = st;
@@ -414,15 +421,17 @@ int decompose_device_rows(truss_ctx *ctx, tr::Arena &A, const tr::RowsIn &in, in
   tr::SupportCfg cfg;
   cfg.sms = ctx->sms;
   cfg.records = true;
+  cfg.in_place = ctx->opts.lists_in_place != 0;
   cfg.pair_cost = ctx->opts.support_pair_cost;
   cfg.range_work = ctx->opts.support_range_work;
   cfg.stage_max = ctx->opts.support_stage_max;
   tr::SupportOut so;
   TR_TRY(tr::run_support(A, g, cfg, &so, s));
-  int2 *pairs = A.get<int2>(so.entries);
+  int2 *pairs = A.get<int2>(tr::list_rest_entries(so));
   int32_t *truss_e = A.get<int32_t>(g.m);
   if (!pairs || !truss_e) return TRUSS_ENOMEM;
-  TR_TRY(tr::run_lists(A, g, cfg, so, pairs, nullptr, s));
+  tr::TriLists lists;
+  TR_TRY(tr::run_lists(A, g, cfg, so, pairs, nullptr, &lists, s));
   tr::PeelCfg pcfg;
   pcfg.sms = ctx->sms;
   pcfg.variant = ctx->opts.peel_variant;
@@ -434,7 +443,7 @@ int decompose_device_rows(truss_ctx *ctx, tr::Arena &A, const tr::RowsIn &in, in
     TR_TRY(tr::pin_edges(g.rows, g.row2e, pinned_rows, pe, g.m, s));
     pcfg.pinned = pe;
   }
-  int rc = tr::run_peel(A, g, so, pairs, pcfg, truss_e, pr, s);
+  int rc = tr::run_peel(A, g, so, lists, pcfg, truss_e, pr, s);
   if (rc != TRUSS_OK) return rc;
   return tr::scatter_rows(g, so.sup, truss_e, sup_rows, truss_rows, s);
 }

@@ -101,12 +101,15 @@ struct SupportOut {
   int64_t records = 0;       // size of the record regions (record indices are below it)
   int2 *tb = nullptr;        // (e_uw, e_vw) records per walked edge e_uv
   int32_t *cuv = nullptr;    // [m] records per edge
+  bool in_place = false;     // the lists keep each edge's own part in its records
 };
 
 struct SupportCfg {
   int block = 256;
   int sms = 0;
   bool records = false;  // also record triangles for the list pass (if memory allows)
+  bool full_lists = false;  // the lists must be whole (the barrier-free peel's layout)
+  bool in_place = false;    // own parts in place whenever records are used
   int pair_cost = 0;      // fixed cost per oriented edge, in out-list entries (0 = default, <0 = none)
   int64_t range_work = 0; // walk cost per range (0 = default)
   int stage_max = 0;      // stage out-lists of at most this many entries (0 = capacity)
@@ -114,12 +117,33 @@ struct SupportCfg {
 
 // Support of every edge: sup = supA + supB (support.cu).
 int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, cudaStream_t s);
-// Triangle lists: pairs[toff[e] .. toff[e]+sup[e]) = the other two edge ids
-// of each triangle of e (support.cu).
-// tids (nullable, only with records): the record index of each entry's
-// triangle, for the barrier-free peel.
+// Where the triangle list of each edge lives: for edge e, the other two
+// edge ids of each triangle of e are own[own_off[e] .. own_off[e] +
+// own_cnt[e]) followed by rest[off[e] .. off[e] + sup[e] - own_cnt[e]).
+// With the own parts in place (SupportOut::in_place), the own part is e's
+// records (the triangles e closes as the walked edge), left where the support
+// walk wrote them, and rest holds only the two partner copies of each
+// triangle; otherwise own_cnt is null and rest[toff[e] ..) holds e's whole
+// list.
+struct TriLists {
+  const int2 *own = nullptr;
+  const int64_t *own_off = nullptr;
+  const int32_t *own_cnt = nullptr;
+  const int2 *rest = nullptr;
+  const int64_t *off = nullptr;
+};
+
+// Entries the lists' `rest` array needs: 2T with the own parts in place,
+// else all 3T.
+inline int64_t list_rest_entries(const SupportOut &so) {
+  return (so.tb && so.in_place) ? so.entries - so.entries / 3 : so.entries;
+}
+
+// Triangle lists (support.cu) into `pairs` (list_rest_entries entries).
+// tids (nullable, only with records and whole lists): the record index of
+// each entry's triangle, for the barrier-free peel.
 int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &so, int2 *pairs,
-              uint32_t *tids, cudaStream_t s);
+              uint32_t *tids, TriLists *out, cudaStream_t s);
 
 // ---------------------------------------------------------------- peel ---
 struct PeelCfg {
@@ -143,7 +167,7 @@ struct PeelResult {
 int run_peel_async(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs,
                    const uint32_t *tids, int64_t ntri, const PeelCfg &cfg, int32_t *truss,
                    PeelResult *out, cudaStream_t s);
-int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, const PeelCfg &cfg,
+int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, const PeelCfg &cfg,
              int32_t *truss, PeelResult *res, cudaStream_t s);
 
 // -------------------------------------------------------------- outputs ---
@@ -205,7 +229,7 @@ int pin_edges(int64_t rows, const int32_t *row2e, const uint8_t *pinned_rows, ui
 int run_core(Arena &A, const Csr &g, int sms, long long wait_ns, int32_t *core_out,
              int32_t *kmax, int32_t *levels, int32_t *subrounds, cudaStream_t s);
 
-int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, double *b_sup,
-                        double *b_lists, cudaStream_t s);
+int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, bool in_place,
+                        double *b_sup, double *b_lists, cudaStream_t s);
 
 }  // namespace tr

@@ -81,14 +81,18 @@ struct PeelCtl {
 
 struct PeelArgs {
   int64_t m;
-  const int64_t *toff;
   const int32_t *sup;
-  const int2 *pairs;
+  // list of e: own[own_off[e] ..] (own_cnt[e] entries), then rest[off[e] ..]
+  const int2 *own;
+  const int64_t *own_off;
+  const int32_t *own_cnt;  // null: no own parts
+  const int2 *rest;
+  const int64_t *off;
   int32_t *res;
   int32_t *stamp;
   int32_t *truss;
   int32_t *alive0, *alive1;
-  int4 *Q0, *Q1;      // frontier work items (edge, count | first << 8, offset lo, hi)
+  int4 *Q0, *Q1;      // frontier work items (make_item)
   int64_t item_cap;   // capacity of Q0 and Q1
   int4 *trace;        // optional: per phase (k, items or -1 for a scan, globaltimer lo/hi)
   int trace_cap;
@@ -98,6 +102,20 @@ struct PeelArgs {
 };
 
 __device__ __forceinline__ int items_of(int len) { return len > 0 ? (len + kItem - 1) / kItem : 1; }
+
+// A work item covers up to kItem consecutive entries of one edge's list:
+// na from its own part at offset oa, then nb from its rest part at ob.
+// Offsets have 42 bits (x = edge, y = na | nb << 5 | first << 10 | the high
+// 10 bits of oa << 11 | those of ob << 21, z / w = the low words of oa / ob).
+constexpr int64_t kOffLimit = (int64_t)1 << 42;
+
+__device__ __forceinline__ int4 make_item(int e, int na, int nb, bool first, int64_t oa,
+                                          int64_t ob) {
+  const uint32_t hi = (uint32_t)na | ((uint32_t)nb << 5) | ((uint32_t)first << 10) |
+                      ((uint32_t)((uint64_t)oa >> 32) & 0x3FFu) << 11 |
+                      ((uint32_t)((uint64_t)ob >> 32) & 0x3FFu) << 21;
+  return make_int4(e, (int)hi, (int)(uint32_t)oa, (int)(uint32_t)ob);
+}
 
 // Per-warp staging buffers in shared memory (counts are warp-uniform).
 struct WarpBuf {
@@ -150,14 +168,19 @@ __device__ __forceinline__ void push_alive(const PeelArgs &a, bool keep, int e, 
 // stamping p with `stamp_val`.  All lanes call it.  Small batches go through
 // the warp's staging buffer; a batch larger than the buffer is written
 // straight to Q with its own reservation.
+template <bool OWN>
 __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, WarpBuf &wb,
                                            int4 *Q, unsigned long long *qctr, int stamp_val) {
   const int lane = lane_id();
-  int n = 0, L = 0;
-  int64_t lb = 0;
+  int n = 0, L = 0, cA = 0;
+  int64_t la = 0, lb = 0;
   if (push) {
     L = __ldg(&a.sup[p]);
-    lb = __ldg(&a.toff[p]);
+    lb = __ldg(&a.off[p]);
+    if (OWN) {
+      cA = __ldg(&a.own_cnt[p]);
+      la = __ldg(&a.own_off[p]);
+    }
     n = items_of(L);
     a.stamp[p] = stamp_val;
   }
@@ -184,15 +207,17 @@ __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, 
     const int Po = __shfl_sync(TR_FULL, P, o);
     const int no = __shfl_sync(TR_FULL, n, o);
     const int Lo = __shfl_sync(TR_FULL, L, o);
+    const int cAo = OWN ? __shfl_sync(TR_FULL, cA, o) : 0;
+    const int64_t lao = OWN ? __shfl_sync(TR_FULL, la, o) : 0;
     const int64_t lbo = __shfl_sync(TR_FULL, lb, o);
     const long long idx = b0 + t;
     if (t < tot && idx < lim) {
       const int it = t - (Po - no);
       const int start = it * kItem;
       const int cnt = Lo > 0 ? min(kItem, Lo - start) : 0;
-      const int64_t off = lbo + start;
-      dst[idx] = make_int4(po, cnt | ((it == 0) << 8), (int)(uint32_t)off,
-                           (int)(uint32_t)((uint64_t)off >> 32));
+      const int na = min(max(cAo - start, 0), cnt);
+      dst[idx] = make_item(po, na, cnt - na, it == 0, lao + start,
+                           lbo + max(start - cAo, 0));
     }
   }
   __syncwarp();
@@ -230,7 +255,7 @@ __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int
 // decrements its partners outside the frontier; a partner whose residual
 // crosses k-1 -> k-2 joins the next frontier.  All loads and atomics of the
 // NE entries are issued before any result is used.
-template <int NE>
+template <int NE, bool OWN>
 __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bool *v,
                                        const int2 *p, int k, int s, WarpBuf &wb, int4 *N,
                                        unsigned long long *qctr, unsigned long long &n_dec) {
@@ -244,22 +269,31 @@ __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bo
     o2[i] = d2[i] ? atomicSub(&a.res[p[i].y], 1) : INT_MAX;
     n_dec += (unsigned long long)(d1[i] + d2[i]);
   }
-  bool any = false;
+  // pending pushes of this lane, bit 2i (p[i].x) and 2i+1 (p[i].y); the
+  // warp pushes one per lane per step through a single push_items site
+  unsigned pend = 0;
 #pragma unroll
-  for (int i = 0; i < NE; i++) any |= (o1[i] == k - 1) || (o2[i] == k - 1);
-  if (__any_sync(TR_FULL, any)) {
+  for (int i = 0; i < NE; i++)
+    pend |= (o1[i] == k - 1 ? 1u : 0u) << (2 * i) | (o2[i] == k - 1 ? 1u : 0u) << (2 * i + 1);
+  while (__any_sync(TR_FULL, pend != 0)) {
+    int q = 0;
+    const bool has = pend != 0;
+    if (has) {
+      const int b = __ffs(pend) - 1;
+      pend &= pend - 1;
 #pragma unroll
-    for (int i = 0; i < NE; i++) {
-      push_items(a, o1[i] == k - 1, p[i].x, wb, N, qctr, s + 1);
-      push_items(a, o2[i] == k - 1, p[i].y, wb, N, qctr, s + 1);
+      for (int i = 0; i < NE; i++)
+        if ((b >> 1) == i) q = (b & 1) ? p[i].y : p[i].x;
     }
+    push_items<OWN>(a, has, q, wb, N, qctr, s + 1);
   }
 }
 
 // MINB = resident blocks per SM the register budget is sized for (1: up to
 // 128 registers per thread, 2: 64); G = work items per 8-lane group per
 // iteration (2 entries per lane per item).
-template <int MINB, int G>
+// OWN: the lists keep own parts in the records (TriLists::own_cnt set).
+template <int MINB, int G, bool OWN>
 __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   const int lane = lane_id();
   const int wib = threadIdx.x >> 5;
@@ -321,7 +355,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         const bool live = e[u] >= 0 && st[u] == 0;
         const bool toF = live && r[u] <= k - 2;
         const bool keep = live && !toF;
-        push_items(a, toF, e[u], wb, F, qf, s);
+        push_items<OWN>(a, toF, e[u], wb, F, qf, s);
         if (compact) push_alive(a, keep, e[u], wb, alive2, qa);
         wmin = min(wmin, __reduce_min_sync(TR_FULL, keep ? r[u] : INT_MAX));
         wlive += __popc(__ballot_sync(TR_FULL, keep));
@@ -377,20 +411,25 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         int ee[2 * G];
         bool vv[2 * G];
         int2 pp[2 * G];
-        int cnt[G];
-        int64_t lb[G];
+        int na[G], cnt[G];
+        int64_t la[G], lb[G];
 #pragma unroll
         for (int g = 0; g < G; g++) {
           const int64_t it = base + g * 4 + grp;
           ee[2 * g] = 0;
+          na[g] = 0;
           cnt[g] = 0;
+          la[g] = 0;
           lb[g] = 0;
           if (it < nCur) {
             const int4 item = __ldcg(&F[it]);
+            const uint32_t hi = (uint32_t)item.y;
             ee[2 * g] = item.x;
-            cnt[g] = item.y & 0xFF;
-            lb[g] = (int64_t)(((uint64_t)(uint32_t)item.w << 32) | (uint32_t)item.z);
-            if ((item.y >> 8) && j == 0) a.truss[item.x] = k;
+            na[g] = OWN ? (int)(hi & 31u) : 0;
+            cnt[g] = na[g] + ((hi >> 5) & 31u);
+            la[g] = OWN ? (int64_t)(((uint64_t)((hi >> 11) & 0x3FFu) << 32) | (uint32_t)item.z) : 0;
+            lb[g] = (int64_t)(((uint64_t)(hi >> 21) << 32) | (uint32_t)item.w);
+            if (((hi >> 10) & 1u) && j == 0) a.truss[item.x] = k;
           }
           ee[2 * g + 1] = ee[2 * g];
         }
@@ -401,8 +440,11 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           r[g] = ha ? __ldcg(&a.res[ee[2 * g]]) : 0;
           // list entries are read once: evict-first, so that the residuals
           // and stamps (re-read at random) keep their place in L2
-          pp[2 * g] = ha ? __ldcs(&a.pairs[lb[g] + j]) : make_int2(0, 0);
-          pp[2 * g + 1] = hb ? __ldcs(&a.pairs[lb[g] + j + 8]) : make_int2(0, 0);
+          const int2 *srcA = j < na[g] ? a.own + la[g] + j : a.rest + lb[g] + (j - na[g]);
+          const int2 *srcB =
+              j + 8 < na[g] ? a.own + la[g] + j + 8 : a.rest + lb[g] + (j + 8 - na[g]);
+          pp[2 * g] = ha ? __ldcs(srcA) : make_int2(0, 0);
+          pp[2 * g + 1] = hb ? __ldcs(srcB) : make_int2(0, 0);
           vv[2 * g] = ha;
           vv[2 * g + 1] = hb;
         }
@@ -412,7 +454,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           vv[2 * g + 1] = vv[2 * g + 1] && r[g] > 0;
           n_entries += (unsigned long long)(vv[2 * g] + vv[2 * g + 1]);
         }
-        charge<2 * G>(a, ee, vv, pp, k, s, wb, N, qn, n_dec);
+        charge<2 * G, OWN>(a, ee, vv, pp, k, s, wb, N, qn, n_dec);
       }
       flush_items(a, wb, N, qn);
       if (!grid_barrier(&ctl->bar, &ctl->err, a.wait_ns)) return;
@@ -471,11 +513,15 @@ __global__ void k_peel_init(int64_t m, const int32_t *sup, const uint8_t *pinned
 
 }  // namespace
 
-int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, const PeelCfg &cfg,
+int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, const PeelCfg &cfg,
              int32_t *truss, PeelResult *out, cudaStream_t s) {
   const int64_t m = g.m;
   *out = PeelResult{};
   if (m == 0) return TRUSS_OK;
+  // item offsets carry 42 bits
+  if (so.entries >= kOffLimit || (L.own_cnt && so.records >= kOffLimit)) return TRUSS_EINVAL;
+  if (so.entries > 0 && (!L.rest || !L.off || (L.own_cnt && (!L.own || !L.own_off))))
+    return TRUSS_EINVAL;
   // items of one sub-round <= sum over its edges of max(1, ceil(sup / kItem))
   const int64_t item_cap = m + so.entries / kItem + 64;
   int32_t *res = A.get<int32_t>(m), *stamp = A.get<int32_t>(m);
@@ -495,23 +541,29 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const int2 *pairs, co
   // per SM; 3: 1 item per group, one block per SM; otherwise (0, 2) the
   // 64-register kernel with 1 item per group and two blocks per SM
   const int variant = cfg.variant == 1 ? 1 : (cfg.variant == 3 ? 3 : 2);
-  const void *kern = variant == 1 ? (const void *)k_peel<1, 2>
-                     : variant == 3 ? (const void *)k_peel<1, 1> : (const void *)k_peel<2, 1>;
-  int occ = 0;
-  if (variant == 1) {
-    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<1, 2>, kPeelBlock, 0));
-  } else if (variant == 3) {
-    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<1, 1>, kPeelBlock, 0));
+  const bool own = L.own_cnt != nullptr;
+  const void *kern;
+  if (own) {
+    kern = variant == 1   ? (const void *)k_peel<1, 2, true>
+           : variant == 3 ? (const void *)k_peel<1, 1, true>
+                          : (const void *)k_peel<2, 1, true>;
   } else {
-    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel<2, 1>, kPeelBlock, 0));
+    kern = variant == 1   ? (const void *)k_peel<1, 2, false>
+           : variant == 3 ? (const void *)k_peel<1, 1, false>
+                          : (const void *)k_peel<2, 1, false>;
   }
+  int occ = 0;
+  TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPeelBlock, 0));
   if (occ < 1) return TRUSS_ECUDA;
   if (variant != 2 && occ > 1) occ = 1;
   PeelArgs a{};
   a.m = m;
-  a.toff = so.toff;
   a.sup = so.sup;
-  a.pairs = pairs;
+  a.own = L.own;
+  a.own_off = L.own_off;
+  a.own_cnt = L.own_cnt;
+  a.rest = L.rest;
+  a.off = L.off ? L.off : so.toff;
   a.res = res;
   a.stamp = stamp;
   a.truss = truss;

@@ -463,20 +463,19 @@ __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
   }
 }
 
-// Dense triangle lists from the per-edge records: e's own records go first
-// (list slots known), the two partners take a slot from their cursors
-// (starting after their own records).
 // Dense triangle lists from the records, in two passes so that the scattered
 // 8-byte list writes of each pass land in a small window of `pairs` that L2
-// can merge into whole sectors before they reach DRAM.  The list of edge x
-// is pairs[toff[x] .. toff[x] + sup[x]); its first cuv[x] entries are the
-// triangles x closes as the walked edge, in record order, and cur[x] hands
-// out the rest.
+// can merge into whole sectors before they reach DRAM.  The first cuv[x]
+// entries of edge x's list are the triangles x closes as the walked edge, in
+// record order: its records themselves, which stay where the walk wrote
+// them, unless the full lists are asked for (then they are copied to
+// pairs[toff[x] ..)).  cur[x] hands out the slots of the rest, the triangles
+// in which x is e_uw or e_vw.
 //
 // Pass 1 (k_lists_from_records, edges in id order = grouped by owner u): for
-// each record (e_uw, e_vw) of walked edge e_uv it writes e_uv's own entry
-// (contiguous) and e_uw's entry; e_uw lies in out(u), whose lists are one
-// contiguous stretch of `pairs`.
+// each record (e_uw, e_vw) of walked edge e_uv it writes e_uw's entry (and,
+// for the full lists, e_uv's own entry); e_uw lies in out(u), whose lists
+// are one contiguous stretch of `pairs`.
 // Pass 2 (k_lists_vw, walked edges grouped by their head v): e_vw's entry;
 // e_vw lies in out(v), so a warp working on v's in-edges writes into v's
 // stretch.
@@ -485,6 +484,7 @@ __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
 // cursor atomics are in flight per lane before any store needs their results.
 constexpr int kListU = 4;
 
+// toff = null: the own parts stay in place and only partner entries are written.
 __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2 *tb,
                                      const int32_t *cuv, const int64_t *toff,
                                      unsigned long long *cur, int2 *pairs, uint32_t *tids,
@@ -495,7 +495,7 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
   for (int64_t base = gw * 32; base < m; base += nw * 32) {
     const int64_t e = base + lane;
     const int c = e < m ? cuv[e] : 0;
-    const int64_t r0 = e < m ? tbpre[e] : 0, l0 = e < m ? toff[e] : 0;
+    const int64_t r0 = e < m ? tbpre[e] : 0, l0 = (e < m && toff) ? toff[e] : 0;
     const int P = warp_incl_scan(c);
     const int total = __shfl_sync(TR_FULL, P, 31);
     for (int t0 = 0; t0 < total; t0 += 32 * kListU) {
@@ -521,8 +521,8 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
 #pragma unroll
       for (int k = 0; k < kListU; k++) {
         if (rec[k].x < 0) continue;
-        if (x1[k] < entries && x2[k] < entries) {
-          pairs[x1[k]] = rec[k];
+        if ((!toff || x1[k] < entries) && x2[k] < entries) {
+          if (toff) pairs[x1[k]] = rec[k];
           pairs[x2[k]] = make_int2(eo[k], rec[k].y);
           if (tids) {
             tids[x1[k]] = ri[k];
@@ -589,12 +589,22 @@ __global__ void k_edge_ids(int64_t m, int32_t *ids) {
     ids[e] = (int32_t)e;
 }
 
-// Cursors for k_lists_from_records: after each edge's own records.
-__global__ void k_cursors_rec(int64_t m, const int64_t *toff, const int32_t *cuv,
+// Cursors for the list passes: the first slot after each edge's own part
+// (base = toff and skip = cuv for the full lists, base = the rest offsets
+// and skip = null with the own parts in place).
+__global__ void k_cursors_rec(int64_t m, const int64_t *base, const int32_t *skip,
                               unsigned long long *cur) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x)
-    cur[e] = (unsigned long long)(toff[e] + cuv[e]);
+    cur[e] = (unsigned long long)(base[e] + (skip ? skip[e] : 0));
+}
+
+// Length of each edge's rest part, sup - cuv (and 0 at e = m, so that the
+// exclusive sum ends with the total).
+__global__ void k_rest_len(int64_t m, const int32_t *sup, const int32_t *cuv, int64_t *len) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    len[e] = e < m ? (int64_t)(sup[e] - cuv[e]) : 0;
 }
 
 __global__ void k_sum(int64_t m, const int32_t *supA, const int32_t *supB, int32_t *sup,
@@ -713,19 +723,32 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
       TR_CUDA(cudaMemcpyAsync(&R, tbpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TR_CUDA(cudaStreamSynchronize(s));
   }
-  // Records need 8 R bytes now and the lists later at most 24 R more, plus
-  // a few words per edge for the list passes; use them only when that fits
-  // in free device memory (else the list pass walks the graph a second time).
+  // Records need 8 R bytes now, and the lists later at most 24 R more when
+  // they are whole, 16 R with the own parts left in the records, plus a few
+  // words per edge for the list passes.  Whole lists when they fit (their
+  // peel reads one stretch per edge), else own parts in place when those
+  // fit, else no records (the list pass walks the graph a second time).
   int2 *recs = nullptr;
   int32_t *cuv = nullptr;
+  bool in_place = false;
   if (cfg.records && R > 0) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
       cudaGetLastError();
       fr = 0;
     }
-    const double need = 32.0 * (double)R + 20.0 * (double)m;
-    if (need * 1.05 < (double)fr + (double)A.unused()) {
+    const double avail = (double)fr + (double)A.unused();
+    const double need_whole = 1.05 * (32.0 * (double)R + 20.0 * (double)m);
+    const double need_in_place = 1.05 * (24.0 * (double)R + 36.0 * (double)m);
+    bool use = false;
+    if (cfg.full_lists) {
+      use = need_whole < avail;
+    } else if (!cfg.in_place && need_whole < avail) {
+      use = true;
+    } else if (need_in_place < avail) {
+      use = in_place = true;
+    }
+    if (use) {
       recs = A.get<int2>(R);
       cuv = A.get<int32_t>(m);
       if (!recs || !cuv) {
@@ -776,30 +799,56 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
   out->records = recs ? R : 0;
   out->tb = recs;
   out->cuv = recs ? cuv : nullptr;
+  out->in_place = recs && in_place;
   return TRUSS_OK;
 }
 
 int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &so, int2 *pairs,
-              uint32_t *tids, cudaStream_t s) {
+              uint32_t *tids, TriLists *out, cudaStream_t s) {
   const int64_t m = g.m;
+  *out = TriLists{};
+  out->rest = pairs;
+  out->off = so.toff;
   if (m == 0 || so.entries == 0) return TRUSS_OK;
   if (so.tb) {
+    const bool in_place = so.in_place;
+    if (tids && in_place) return TRUSS_EINVAL;  // triangle ids come with whole lists
     unsigned long long *cur = A.get<unsigned long long>(m);
     int *err = A.get<int>(1);
     if (!cur || !err) return TRUSS_ENOMEM;
     TR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    k_cursors_rec<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.cuv, cur);
-    TR_LAUNCHED();
+    const int64_t rest = list_rest_entries(so);
+    if (in_place) {
+      int64_t *len = A.get<int64_t>(m + 1), *roff = A.get<int64_t>(m + 1);
+      if (!len || !roff) return TRUSS_ENOMEM;
+      k_rest_len<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, so.sup, so.cuv, len);
+      TR_LAUNCHED();
+      size_t tb = 0;
+      TR_TRY(exclusive_sum_i64(nullptr, &tb, len, roff, m + 1, s));
+      void *tmp = A.alloc(tb);
+      if (!tmp) return TRUSS_ENOMEM;
+      TR_TRY(exclusive_sum_i64(tmp, &tb, len, roff, m + 1, s));
+      k_cursors_rec<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, roff, nullptr, cur);
+      TR_LAUNCHED();
+      out->own = so.tb;
+      out->own_off = so.tbpre;
+      out->own_cnt = so.cuv;
+      out->off = roff;
+    } else {
+      k_cursors_rec<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.cuv, cur);
+      TR_LAUNCHED();
+    }
     // pass 2 walks the edges grouped by head (the support walk's index)
     const int32_t *inedge = so.inedge;
     int dev = 0, sms = cfg.sms;
     TR_CUDA(cudaGetDevice(&dev));
     if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    k_lists_from_records<<<sms * 8, 256, 0, s>>>(m, so.tbpre, so.tb, so.cuv, so.toff, cur, pairs,
-                                                 tids, so.entries, err);
+    k_lists_from_records<<<sms * 8, 256, 0, s>>>(m, so.tbpre, so.tb, so.cuv,
+                                                 in_place ? nullptr : so.toff, cur, pairs, tids,
+                                                 rest, err);
     TR_LAUNCHED();
     k_lists_vw<<<sms * 8, 256, 0, s>>>(m, inedge, so.tbpre, so.tb, so.cuv, cur, pairs, tids,
-                                       so.entries, err);
+                                       rest, err);
     TR_LAUNCHED();
     int h_err = 0;
     TR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -894,8 +943,8 @@ __global__ void k_count_list_walk(int64_t n, const int64_t *offp, const int32_t 
 // Algorithmic bytes of the support pass: walk bytes + per triangle the
 // read-modify-write of e_uw's count (8 B) and, when recording, its 8-B
 // record.  Of the list pass: see below.
-int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, double *b_sup,
-                        double *b_lists, cudaStream_t s) {
+int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, bool in_place,
+                        double *b_sup, double *b_lists, cudaStream_t s) {
   unsigned long long *acc = A.get<unsigned long long>(1);
   if (!acc) return TRUSS_ENOMEM;
   TR_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
@@ -913,13 +962,17 @@ int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records,
     TR_CUDA(cudaMemcpyAsync(&hl, acc, sizeof(hl), cudaMemcpyDeviceToHost, s));
     TR_CUDA(cudaStreamSynchronize(s));
   }
-  // lists from records: the record read by both passes, three entries, two
-  // cursor RMWs (56 B), and per edge the cursor set-up and both passes'
-  // offset/count reads (56 B; the head-order sort is not counted); lists by
-  // a second walk: the walk again plus 60 B per triangle
+  // whole lists from records: the record read by both passes, three
+  // entries, two cursor RMWs (56 B per triangle), and per edge the cursor
+  // set-up and both passes' offset/count reads (56 B; the head-order sort is
+  // not counted).  Own parts in place: two entries (48 B per triangle), and
+  // per edge the rest lengths and their scan (32 B), the cursor set-up
+  // (16 B) and both passes' reads (28 B).  Lists by a second walk: the walk
+  // again plus 60 B per triangle.
   *b_sup = (double)h + (records ? 16.0 : 8.0) * (double)triangles;
-  *b_lists = records ? 56.0 * (double)triangles + 56.0 * (double)g.m
-                     : (double)hl + 60.0 * (double)triangles;
+  *b_lists = !records  ? (double)hl + 60.0 * (double)triangles
+             : in_place ? 48.0 * (double)triangles + 76.0 * (double)g.m
+                        : 56.0 * (double)triangles + 56.0 * (double)g.m;
   return TRUSS_OK;
 }
 

@@ -42,7 +42,7 @@ class truss_opts(ctypes.Structure):
                 ("count_bytes", ctypes.c_int32), ("support_stage_max", ctypes.c_int32),
                 ("peel_variant", ctypes.c_int32), ("support_range_work", ctypes.c_int32),
                 ("support_pair_cost", ctypes.c_int32), ("lists_by_walk", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("lists_in_place", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class truss_run_stats(ctypes.Structure):
@@ -55,12 +55,12 @@ class truss_run_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("bytes_support", ctypes.c_double),
                 ("bytes_lists", ctypes.c_double), ("bytes_peel", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("candidates", ctypes.c_int64),
-                ("rounds", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("lists_layout", ctypes.c_int32),
                 ("peel_entries", ctypes.c_int64), ("peel_decrements", ctypes.c_int64),
                 ("peel_scanned", ctypes.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved0"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class truss_serve_opts(ctypes.Structure):

@@ -55,7 +55,7 @@ def test_search_finds_the_separable_optimum():
 
     opts, ms, calls = A.search(run, reps=2, same=lambda a, b: a == b)
     assert opts == {"support_range_work": 8192, "support_stage_max": 128,
-                    "support_pair_cost": 16, "peel_variant": 1}
+                    "support_pair_cost": 16, "peel_variant": 1, "lists_in_place": 0}
     assert ms["ms_support"] == 10.0 and ms["ms_peel"] == 5.0
     distinct = 1 + sum(len(v) - 1 for v in A.SPACE.values())
     assert calls == 2 * distinct == len(seen)

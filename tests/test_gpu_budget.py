@@ -85,3 +85,20 @@ def test_budget_with_host_buffers_and_duplicates(ctx):
     ref = oracle.truss(n, src, dst)
     assert np.array_equal(sup, ref.support) and np.array_equal(tr, ref.truss)
     assert k == ref.kmax
+
+
+@pytest.mark.parametrize("name,case,budget", CASES[::2],
+                         ids=[f"{c[0]}-b{c[2]}" for c in CASES[::2]])
+def test_budget_parity_own_parts_in_place(name, case, budget):
+    """The neighbourhood subgraphs' lists with each edge's own part left in
+    the records (truss_opts.lists_in_place)."""
+    from paper_1205_6693_gb300 import truss as T
+    c = T.Context(0, lists_in_place=1)
+    try:
+        n, src, dst = case
+        sup, tr, k, st = gpu_budget(c, n, src, dst, budget)
+        ref = oracle.truss(n, src, dst)
+        assert np.array_equal(sup, ref.support) and np.array_equal(tr, ref.truss)
+        assert k == ref.kmax
+    finally:
+        c.close()

@@ -289,6 +289,56 @@ def test_lists_by_second_walk():
         c.close()
 
 
+def _in_place_cases():
+    yield "tiny", graphgen.tiny()
+    for sc, seed in ((12, 3), (15, 8)):
+        s, d = graphgen.rmat_raw(sc, 16 << sc, seed=seed)
+        yield f"rmat{sc}", (1 << sc, s, d)
+    n = 4000
+    s, d = graphgen.er(n, 16000, seed=23)
+    perm = graphgen.permutation(n, seed=23, stream=1)
+    s, d = graphgen.add_cliques(s, d, perm[:120], [4, 17, 18, 33, 47])
+    yield "er+cliques", (n, s, d)
+
+
+IN_PLACE_CASES = list(_in_place_cases())
+
+
+@pytest.mark.parametrize("variant", [0, 1, 3])
+@pytest.mark.parametrize("name,case", IN_PLACE_CASES, ids=[c[0] for c in IN_PLACE_CASES])
+def test_lists_own_parts_in_place(name, case, variant):
+    """Lists that leave each edge's own triangles in the support walk's
+    records (truss_opts.lists_in_place): the peel reads every list in two
+    stretches, and a work item may span both.  Clique sizes 17, 18, 33 and 47
+    give supports on both sides of the 16-entry item size."""
+    from paper_1205_6693_gb300 import truss as T
+    c = T.Context(0, lists_in_place=1, peel_variant=variant)
+    try:
+        n, src, dst = case
+        assert_same(c, n, src, dst)
+        assert c.stats()["lists_layout"] == 3
+    finally:
+        c.close()
+
+
+def test_lists_layout_reported():
+    """truss_last_stats names the list layout each call used."""
+    from paper_1205_6693_gb300 import truss as T
+    n, src, dst = graphgen.tiny()
+    for kw, want in (({}, 2), ({"lists_by_walk": 1}, 1), ({"lists_in_place": 1}, 3),
+                     ({"lists_in_place": 1, "peel_variant": 4}, 2)):
+        c = T.Context(0, **kw)
+        try:
+            assert_same(c, n, src, dst)
+            assert c.stats()["lists_layout"] == want, kw
+            s = torch.from_numpy(np.ascontiguousarray(src, np.int32)).to("cuda:0")
+            d = torch.from_numpy(np.ascontiguousarray(dst, np.int32)).to("cuda:0")
+            c.support(n, s, d, torch.empty_like(s))
+            assert c.stats()["lists_layout"] == 0
+        finally:
+            c.close()
+
+
 @pytest.fixture(scope="module")
 def ctx_async():
     from paper_1205_6693_gb300 import truss as T
