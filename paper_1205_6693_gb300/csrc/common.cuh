@@ -109,36 +109,55 @@ __device__ __forceinline__ long long warp_append64(bool pred, unsigned long long
   return (long long)(base + __popc(mask & ((1u << lane_id()) - 1u)));
 }
 
+// Acquire-release atomic add and acquire load at GPU scope.
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long *p,
+                                                                   unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+               : "=l"(old)
+               : "l"(p), "l"(v)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid-wide barrier of a cooperative launch, with a time limit.  Arrival is
 // one atomic increment of `bar`, a counter that is never reset: the block
 // whose increment returned `old` waits until the counter reaches the next
 // multiple of the grid size (every block arrives exactly once per barrier,
-// so one barrier's arrivals are gridDim.x consecutive values).  A wait longer
-// than wait_ns records TRUSS_ETIMEOUT in *err.  Returns false if any block
-// has recorded an error, so that every block leaves at its next barrier.
+// so one barrier's arrivals are gridDim.x consecutive values).  The block's
+// writes are published by the __syncthreads and the release half of the
+// increment, and the other blocks' writes are seen through the acquire
+// loads of the wait (or the acquire half of the last increment).  A wait
+// longer than wait_ns records TRUSS_ETIMEOUT in *err.  Returns false if any
+// block has recorded an error, so that every block leaves at its next
+// barrier.
 __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err,
                                              long long wait_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long old = atomicAdd(bar, 1ull);
+    const unsigned long long old = atom_add_acq_rel_gpu(bar, 1ull);
     const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
     if (old + 1 != target) {
-      volatile unsigned long long *vb = bar;
       volatile int *verr = err;
       const unsigned long long t0 = global_ns();
-      int spins = 0;
-      while (*vb < target) {
-        if (++spins > 32) __nanosleep(32);
-        if (*verr != 0) break;
-        if ((long long)(global_ns() - t0) > wait_ns) {
-          atomicExch(err, TRUSS_ETIMEOUT);
-          break;
+      for (unsigned spins = 1; ld_acquire_gpu(bar) < target; spins++) {
+        if (spins > 32) __nanosleep(32);
+        if ((spins & 15) == 0) {
+          if (*verr != 0) break;
+          if ((long long)(global_ns() - t0) > wait_ns) {
+            atomicExch(err, TRUSS_ETIMEOUT);
+            break;
+          }
         }
       }
     }
-    __threadfence();
     s_ok = (*(volatile int *)err) == 0;
   }
   __syncthreads();

@@ -281,10 +281,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_core(CoreArgs a) {
         int old[2];
 #pragma unroll
         for (int q = 0; q < 2; q++) old[q] = dec[q] ? atomicSub(&a.deg[w[q]], 1) : INT_MIN;
-        const bool any = (old[0] == k + 1) || (old[1] == k + 1);
-        if (__any_sync(TR_FULL, any)) {
-#pragma unroll
-          for (int q = 0; q < 2; q++) push_items(a, old[q] == k + 1, w[q], wb, N, qn, s + 1);
+        // one push_items site: each step pushes one pending neighbour per lane
+        unsigned pend = (old[0] == k + 1 ? 1u : 0u) | (old[1] == k + 1 ? 2u : 0u);
+        while (__any_sync(TR_FULL, pend != 0)) {
+          const bool has = pend != 0;
+          const int b = has ? __ffs(pend) - 1 : 0;
+          pend &= pend - 1;
+          push_items(a, has, b ? w[1] : w[0], wb, N, qn, s + 1);
         }
       }
       flush_items(a, wb, N, qn);

@@ -350,16 +350,29 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         st[u] = e[u] >= 0 ? __ldcg(&a.stamp[e[u]]) : 1;
         r[u] = e[u] >= 0 ? __ldcg(&a.res[e[u]]) : 0;
       }
+      unsigned pend = 0;  // entries of this lane that join the frontier
 #pragma unroll
       for (int u = 0; u < kScanU; u++) {
         const bool live = e[u] >= 0 && st[u] == 0;
         const bool toF = live && r[u] <= k - 2;
         const bool keep = live && !toF;
-        push_items<OWN>(a, toF, e[u], wb, F, qf, s);
+        pend |= (toF ? 1u : 0u) << u;
         if (compact) push_alive(a, keep, e[u], wb, alive2, qa);
         wmin = min(wmin, __reduce_min_sync(TR_FULL, keep ? r[u] : INT_MAX));
         wlive += __popc(__ballot_sync(TR_FULL, keep));
         n_scan += (e[u] >= 0);
+      }
+      while (__any_sync(TR_FULL, pend != 0)) {
+        int q = 0;
+        const bool has = pend != 0;
+        if (has) {
+          const int b = __ffs(pend) - 1;
+          pend &= pend - 1;
+#pragma unroll
+          for (int u = 0; u < kScanU; u++)
+            if (b == u) q = e[u];
+        }
+        push_items<OWN>(a, has, q, wb, F, qf, s);
       }
     }
     flush_items(a, wb, F, qf);
