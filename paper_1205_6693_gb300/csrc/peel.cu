@@ -318,6 +318,15 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   int64_t nAlive = a.m;
   bool compact = false;  // rewrite the alive list during this scan
   unsigned long long n_entries = 0, n_dec = 0, n_scan = 0;
+  // this warp's first work items of the coming sub-round, loaded right after
+  // the barrier together with the item count instead of after it
+  int4 pre[G];
+  const int64_t it0 = gwarp * 4 * G + (lane >> 3);
+  auto prefetch = [&](const int4 *Q) {
+#pragma unroll
+    for (int g = 0; g < G; g++)
+      pre[g] = it0 + g * 4 < a.item_cap ? __ldcg(&Q[it0 + g * 4]) : make_int4(0, 0, 0, 0);
+  };
 
   for (;;) {
     if (a.k_stop > 0 && k > a.k_stop) break;  // k is the same in every block
@@ -390,6 +399,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
     }
     if (!grid_barrier(&ctl->bar, &ctl->err, a.wait_ns)) return;
     ph++;
+    prefetch(F);
     const int minres = __ldcg(&ctl->minres[slot]);
     const int64_t live = __ldcg(&ctl->live[slot]);
     const int64_t nF = (int64_t)__ldcg(qf);
@@ -435,7 +445,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           la[g] = 0;
           lb[g] = 0;
           if (it < nCur) {
-            const int4 item = __ldcg(&F[it]);
+            const int4 item = base == gwarp * 4 * G ? pre[g] : __ldcg(&F[it]);
             const uint32_t hi = (uint32_t)item.y;
             ee[2 * g] = item.x;
             na[g] = OWN ? (int)(hi & 31u) : 0;
@@ -472,6 +482,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
       flush_items(a, wb, N, qn);
       if (!grid_barrier(&ctl->bar, &ctl->err, a.wait_ns)) return;
       ph++;
+      prefetch(N);
       const int64_t nN = (int64_t)__ldcg(qn);
       s++;
       if (leader) ctl->subrounds++;
