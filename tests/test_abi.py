@@ -129,3 +129,39 @@ def test_header_is_plain_c_and_links(tmp_path):
     assert out.returncode == 0
     rc = int(out.stdout.split()[0])
     assert rc in (T.TRUSS_OK, T.TRUSS_ECUDA, T.TRUSS_EINVAL)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the C header's size and the
+    same name and offset for each field (a C program compiled against
+    include/truss.h prints them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    from paper_1205_6693_gb300 import truss as T
+    structs = [T.truss_opts, T.truss_run_stats, T.truss_serve_opts, T.truss_req_stats,
+               T.truss_serve_stats]
+    lines = ['#include "truss.h"', "#include <stddef.h>", "#include <stdio.h>",
+             "int main(void) {"]
+    for S in structs:
+        c = S.__name__
+        lines.append(f'  printf("{c} size %zu\\n", sizeof({c}));')
+        for f, _ in S._fields_:
+            lines.append(f'  printf("{c} {f} %zu\\n", offsetof({c}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I",
+                           os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60, check=True)
+    got = {}
+    for ln in out.stdout.splitlines():
+        c, f, v = ln.split()
+        got[(c, f)] = int(v)
+    for S in structs:
+        c = S.__name__
+        assert got[(c, "size")] == ctypes.sizeof(S), c
+        for f, _ in S._fields_:
+            assert got[(c, f)] == getattr(S, f).offset, (c, f)
