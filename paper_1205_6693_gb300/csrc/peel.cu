@@ -41,12 +41,16 @@
 // leaves a barrier early therefore never appends to a counter that a slow
 // block has still to read.
 //
-// Edge state is one int per edge, stamp[e]: 0 = alive, s = in the frontier of
-// sub-round s, 0 < stamp < s = removed earlier.  A partner pushed during
-// sub-round s is stamped s+1, which reads as alive during s, so one grid
-// barrier per sub-round suffices.  res[e] of a frontier edge is never touched
-// during its sub-round and equals the number of its still-alive triangles,
-// so a frontier edge with res 0 skips its list.
+// Edge state is one 16-bit tag per edge, stamp[e]: 0 = alive, tag(s) = in
+// the frontier of sub-round s, any other value = removed earlier.  A partner
+// pushed during sub-round s is tagged tag(s+1), which reads as alive during
+// s, so one grid barrier per sub-round suffices.  Tags repeat every 65,534
+// sub-rounds, so at least every 32,768 sub-rounds one extra grid-wide pass
+// rewrites every tag but the current frontier's to kDead.  (A 2-byte stamp
+// leaves more of L2 to the residuals, which are read at random.)  res[e] of
+// a frontier edge is never touched during its sub-round and equals the
+// number of its still-alive triangles, so a frontier edge with res 0 skips
+// its list.
 //
 // Every grid barrier waits at most `wait_ns` (globaltimer); on timeout the
 // kernel records TRUSS_ETIMEOUT and all blocks return at their next barrier.
@@ -89,7 +93,8 @@ struct PeelArgs {
   const int2 *rest;
   const int64_t *off;
   int32_t *res;
-  int32_t *stamp;
+  uint16_t *stamp;
+  int retag;  // sub-rounds between tag rewrites (1 .. kRetagMax)
   int32_t *truss;
   int32_t *alive0, *alive1;
   int4 *Q0, *Q1;      // frontier work items (make_item)
@@ -102,6 +107,12 @@ struct PeelArgs {
 };
 
 __device__ __forceinline__ int items_of(int len) { return len > 0 ? (len + kItem - 1) / kItem : 1; }
+
+constexpr int kTagMod = 65534;
+constexpr int kRetagMax = 32768;
+constexpr uint16_t kDead = 0xFFFF;
+// Tag of sub-round s >= 1: 1 .. kTagMod.
+__device__ __forceinline__ uint16_t tag_of(int s) { return (uint16_t)(1 + (s - 1) % kTagMod); }
 
 // A work item covers up to kItem consecutive entries of one edge's list:
 // na from its own part at offset oa, then nb from its rest part at ob.
@@ -165,12 +176,12 @@ __device__ __forceinline__ void push_alive(const PeelArgs &a, bool keep, int e, 
 }
 
 // Append the work items of edge p (for each lane with `push`) to queue Q,
-// stamping p with `stamp_val`.  All lanes call it.  Small batches go through
+// stamping p with tag `tagv`.  All lanes call it.  Small batches go through
 // the warp's staging buffer; a batch larger than the buffer is written
 // straight to Q with its own reservation.
 template <bool OWN>
 __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, WarpBuf &wb,
-                                           int4 *Q, unsigned long long *qctr, int stamp_val) {
+                                           int4 *Q, unsigned long long *qctr, uint16_t tagv) {
   const int lane = lane_id();
   int n = 0, L = 0, cA = 0;
   int64_t la = 0, lb = 0;
@@ -182,7 +193,7 @@ __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, 
       la = __ldg(&a.own_off[p]);
     }
     n = items_of(L);
-    a.stamp[p] = stamp_val;
+    a.stamp[p] = tagv;
   }
   const int P = warp_incl_scan(n);
   const int tot = __shfl_sync(TR_FULL, P, 31);
@@ -227,8 +238,9 @@ __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, 
 // Decide whether frontier edge e charges the triangle {e, p1, p2} in
 // sub-round s: all three edges alive, and e the lowest-id frontier edge among
 // them.  d1 / d2 = decrement p1 / p2 (the partners not in the frontier).
-__device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int2 pr, int s,
-                                       bool &d1, bool &d2) {
+// ts / tn = tag(s) / tag(s+1).
+__device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int2 pr, int ts,
+                                       int tn, bool &d1, bool &d2) {
   d1 = d2 = false;
   if (!valid) return;
   const int p1 = pr.x, p2 = pr.y;
@@ -237,9 +249,9 @@ __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int
     return;
   }
   const int s1 = __ldcg(&a.stamp[p1]), s2 = __ldcg(&a.stamp[p2]);
-  const bool dead1 = s1 > 0 && s1 < s, dead2 = s2 > 0 && s2 < s;
+  const bool dead1 = s1 != 0 && s1 != ts && s1 != tn, dead2 = s2 != 0 && s2 != ts && s2 != tn;
   if (dead1 || dead2) return;
-  const bool in1 = s1 == s, in2 = s2 == s;
+  const bool in1 = s1 == ts, in2 = s2 == ts;
   if (!in1 && !in2) {
     d1 = true;
     d2 = true;
@@ -257,11 +269,12 @@ __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int
 // NE entries are issued before any result is used.
 template <int NE, bool OWN>
 __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bool *v,
-                                       const int2 *p, int k, int s, WarpBuf &wb, int4 *N,
-                                       unsigned long long *qctr, unsigned long long &n_dec) {
+                                       const int2 *p, int k, int ts, int tn, WarpBuf &wb,
+                                       int4 *N, unsigned long long *qctr,
+                                       unsigned long long &n_dec) {
   bool d1[NE], d2[NE];
 #pragma unroll
-  for (int i = 0; i < NE; i++) decide(a, v[i], e[i], p[i], s, d1[i], d2[i]);
+  for (int i = 0; i < NE; i++) decide(a, v[i], e[i], p[i], ts, tn, d1[i], d2[i]);
   int o1[NE], o2[NE];
 #pragma unroll
   for (int i = 0; i < NE; i++) {
@@ -285,7 +298,7 @@ __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bo
       for (int i = 0; i < NE; i++)
         if ((b >> 1) == i) q = (b & 1) ? p[i].y : p[i].x;
     }
-    push_items<OWN>(a, has, q, wb, N, qctr, s + 1);
+    push_items<OWN>(a, has, q, wb, N, qctr, (uint16_t)tn);
   }
 }
 
@@ -327,9 +340,26 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
     for (int g = 0; g < G; g++)
       pre[g] = it0 + g * 4 < a.item_cap ? __ldcg(&Q[it0 + g * 4]) : make_int4(0, 0, 0, 0);
   };
+  // Every a.retag sub-rounds (checked at the start of each phase, the same in
+  // every block): tags other than the current frontier's become kDead.  A
+  // tag left on a removed edge is then from the last a.retag sub-rounds, so
+  // it never equals tag(s) or tag(s+1) of a later sub-round by wrapping.
+  int last_retag = 0;
+  auto retag = [&]() -> bool {
+    if (s - last_retag < a.retag) return true;
+    last_retag = s;
+    const uint16_t keep = tag_of(s);
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.m; e += nt) {
+      const uint16_t t = __ldcg(&a.stamp[e]);
+      if (t != 0 && t != keep) a.stamp[e] = kDead;
+    }
+    return grid_barrier(&ctl->bar, &ctl->err, a.wait_ns);
+  };
 
   for (;;) {
     if (a.k_stop > 0 && k > a.k_stop) break;  // k is the same in every block
+    if (!retag()) return;
     // ------------------------------------------------------------ scan ---
     if (leader && a.trace && ctl->ntrace < a.trace_cap) {
       const unsigned long long t = global_ns();
@@ -381,7 +411,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           for (int u = 0; u < kScanU; u++)
             if (b == u) q = e[u];
         }
-        push_items<OWN>(a, has, q, wb, F, qf, s);
+        push_items<OWN>(a, has, q, wb, F, qf, tag_of(s));
       }
     }
     flush_items(a, wb, F, qf);
@@ -419,6 +449,8 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
     // --------------------------------------------------------- sub-rounds ---
     int64_t nCur = nF;
     for (;;) {
+      if (!retag()) return;
+      const int ts = tag_of(s), tn = tag_of(s + 1);
       if (leader && a.trace && ctl->ntrace < a.trace_cap) {
         const unsigned long long t = global_ns();
         a.trace[ctl->ntrace++] = make_int4(k, (int)min(nCur, (int64_t)INT_MAX),
@@ -477,7 +509,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           vv[2 * g + 1] = vv[2 * g + 1] && r[g] > 0;
           n_entries += (unsigned long long)(vv[2 * g] + vv[2 * g + 1]);
         }
-        charge<2 * G, OWN>(a, ee, vv, pp, k, s, wb, N, qn, n_dec);
+        charge<2 * G, OWN>(a, ee, vv, pp, k, ts, tn, wb, N, qn, n_dec);
       }
       flush_items(a, wb, N, qn);
       if (!grid_barrier(&ctl->bar, &ctl->err, a.wait_ns)) return;
@@ -519,7 +551,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
 constexpr int kPinnedRes = INT_MAX / 4;
 
 __global__ void k_peel_init(int64_t m, const int32_t *sup, const uint8_t *pinned, int32_t *res,
-                            int32_t *stamp, int32_t *alive, int32_t *truss, PeelCtl *ctl) {
+                            uint16_t *stamp, int32_t *alive, int32_t *truss, PeelCtl *ctl) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
     res[e] = (pinned && pinned[e]) ? kPinnedRes : sup[e];
@@ -548,7 +580,8 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, co
     return TRUSS_EINVAL;
   // items of one sub-round <= sum over its edges of max(1, ceil(sup / kItem))
   const int64_t item_cap = m + so.entries / kItem + 64;
-  int32_t *res = A.get<int32_t>(m), *stamp = A.get<int32_t>(m);
+  int32_t *res = A.get<int32_t>(m);
+  uint16_t *stamp = A.get<uint16_t>(m);
   int32_t *al0 = A.get<int32_t>(m), *al1 = A.get<int32_t>(m);
   int4 *Q0 = A.get<int4>(item_cap), *Q1 = A.get<int4>(item_cap);
   PeelCtl *ctl = A.get<PeelCtl>(1);
@@ -590,6 +623,11 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, co
   a.off = L.off ? L.off : so.toff;
   a.res = res;
   a.stamp = stamp;
+  a.retag = kRetagMax;
+  if (const char *rt = getenv("TRUSS_PEEL_RETAG")) {  // testing: rewrite tags more often
+    const int v = atoi(rt);
+    a.retag = v < 1 ? 1 : v > kRetagMax ? kRetagMax : v;
+  }
   a.truss = truss;
   a.alive0 = al0;
   a.alive1 = al1;

@@ -339,6 +339,23 @@ def test_lists_layout_reported():
             c.close()
 
 
+def test_peel_tag_rewrite(monkeypatch):
+    """The peel's 16-bit edge tags repeat every 65,534 sub-rounds, so the
+    kernel rewrites stale ones periodically; forced every 1 and every 3
+    sub-rounds (TRUSS_PEEL_RETAG), the results stay bit-exact."""
+    from paper_1205_6693_gb300 import truss as T
+    cases = [graphgen.tiny(), (1 << 13, *graphgen.rmat_raw(13, 16 << 13, seed=4)),
+             IN_PLACE_CASES[-1][1]]
+    for period in ("1", "3"):
+        monkeypatch.setenv("TRUSS_PEEL_RETAG", period)
+        c = T.Context(0)
+        try:
+            for n, src, dst in cases:
+                assert_same(c, n, src, dst)
+        finally:
+            c.close()
+
+
 @pytest.fixture(scope="module")
 def ctx_async():
     from paper_1205_6693_gb300 import truss as T
