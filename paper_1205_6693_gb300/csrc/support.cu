@@ -236,6 +236,22 @@ __device__ __forceinline__ int find_in_out(int w, const int32_t *Ls, const unsig
   }
 }
 
+// Walks of at most kShortWalk entries are spread over the lanes, several
+// edges per warp step; longer ones take the warp one edge at a time.
+constexpr int kShortWalk = 128;
+constexpr int kFlatU = 4;  // flattened steps whose loads are issued together
+
+// One hit of the walk: triangle (u, v, w) with e_uw = euw and e_vw at
+// position q of out(v), recorded at slot `slot` of e_uv's region.
+template <bool STAGED>
+__device__ __forceinline__ void count_hit(const SupVArgs &a, int32_t *Cs, int64_t bv, int q,
+                                          int64_t euw, int64_t slot) {
+  if (STAGED) atomicAdd(&Cs[q], 1);
+  else atomicAdd(&a.supB[bv + q], 1);
+  atomicAdd(&a.supA[euw], 1);
+  if (a.tb) a.tb[slot] = make_int2((int)euw, (int)(bv + q));
+}
+
 // The in-edges inedge[i0 .. i1) of head v (bv = offp[v], dv = |out(v)|).
 template <bool STAGED>
 __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t i1, int64_t bv,
@@ -251,8 +267,65 @@ __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t
     const int64_t uend = valid ? __ldg(&a.offp[u + 1]) : 0;
     const int len = valid ? (int)(uend - (int64_t)e - 1) : 0;  // entries of out(u) after v
     const int64_t rb = (valid && a.tb) ? __ldg(&a.tbpre[e]) : 0;
-    const int nv = (int)min((int64_t)32, i1 - c0);
-    for (int o = 0; o < nv; o++) {
+
+    // short walks, flattened: step t of the warp is entry t - base(o) of
+    // the walk of lane o = the owner of t (base = exclusive prefix of sl)
+    const bool shrt = len <= kShortWalk;
+    const int sl = shrt ? len : 0;
+    const int P = warp_incl_scan(sl);
+    const int total = __shfl_sync(TR_FULL, P, 31);
+    int mycnt = 0;  // triangles found so far for this lane's (short) edge
+    for (int t0 = 0; t0 < total; t0 += 32 * kFlatU) {
+      int w[kFlatU], own[kFlatU], bo[kFlatU];
+#pragma unroll
+      for (int k = 0; k < kFlatU; k++) {
+        const int t = t0 + k * 32 + lane;
+        const bool act = t < total;
+        own[k] = warp_owner(P, act ? t : total - 1);
+        const int Po = __shfl_sync(TR_FULL, P, own[k]), so = __shfl_sync(TR_FULL, sl, own[k]);
+        const int eo = __shfl_sync(TR_FULL, e, own[k]);
+        bo[k] = Po - so;
+        w[k] = act ? __ldg(&a.adjp[(int64_t)eo + 1 + (t - bo[k])]) : INT_MAX;
+      }
+#pragma unroll
+      for (int k = 0; k < kFlatU; k++) {
+        const int tr = t0 + k * 32;  // step of lane 0 in this round
+        const int q =
+            w[k] <= vmax ? find_in_out<STAGED>(w[k], Ls, Hs, S, sh, a.adjp + bv, dv) : -1;
+        const unsigned hm = __ballot_sync(TR_FULL, q >= 0);
+        if (hm == 0) continue;
+        const int prior = __shfl_sync(TR_FULL, mycnt, own[k]);
+        const int64_t tbase = __shfl_sync(TR_FULL, rb, own[k]);
+        const int eo = __shfl_sync(TR_FULL, e, own[k]);
+        if (q >= 0) {
+          // lanes of this round that walk the same edge: steps [bo, bo + so)
+          const int lo = max(bo[k] - tr, 0);
+          const unsigned below = hm & lt & ~((1u << lo) - 1u);
+          const int64_t euw = (int64_t)eo + 1 + (tr + lane - bo[k]);
+          count_hit<STAGED>(a, Cs, bv, q, euw, tbase + prior + __popc(below));
+        }
+        // owners add this round's hits of their own walk
+        if (sl > 0) {
+          const int lo = P - sl - tr, hi = P - 1 - tr;
+          if (hi >= 0 && lo <= 31) {
+            const int l0 = max(lo, 0), l1 = min(hi, 31);
+            const unsigned seg = (l1 == 31 ? 0xFFFFFFFFu : ((1u << (l1 + 1)) - 1u)) &
+                                 ~((1u << l0) - 1u);
+            mycnt += __popc(hm & seg);
+          }
+        }
+      }
+    }
+    if (valid && shrt) {
+      if (a.tb) a.cuv[e] = mycnt;
+      if (mycnt) atomicAdd(&a.supA[e], mycnt);
+    }
+
+    // long walks: the whole warp on one edge, stopping past max out(v)
+    unsigned lm = __ballot_sync(TR_FULL, valid && !shrt);
+    while (lm) {
+      const int o = __ffs(lm) - 1;
+      lm &= lm - 1;
       const int eo = __shfl_sync(TR_FULL, e, o);
       const int olen = __shfl_sync(TR_FULL, len, o);
       const int64_t tbase = __shfl_sync(TR_FULL, rb, o);
@@ -270,14 +343,9 @@ __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t
           const int q =
               w[k] <= vmax ? find_in_out<STAGED>(w[k], Ls, Hs, S, sh, a.adjp + bv, dv) : -1;
           const unsigned hm = __ballot_sync(TR_FULL, q >= 0);
-          if (q >= 0) {
-            const int64_t euw = start + t0 + k * 32 + lane;
-            if (STAGED) atomicAdd(&Cs[q], 1);
-            else atomicAdd(&a.supB[bv + q], 1);
-            atomicAdd(&a.supA[euw], 1);
-            if (a.tb)
-              a.tb[tbase + cnt + __popc(hm & lt)] = make_int2((int)euw, (int)(bv + q));
-          }
+          if (q >= 0)
+            count_hit<STAGED>(a, Cs, bv, q, start + t0 + k * 32 + lane,
+                              tbase + cnt + __popc(hm & lt));
           cnt += __popc(hm);
         }
         // out(u) is sorted: past max out(v) nothing can match
