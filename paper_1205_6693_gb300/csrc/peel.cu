@@ -271,7 +271,7 @@ template <int NE, bool OWN>
 __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bool *v,
                                        const int2 *p, int k, int ts, int tn, WarpBuf &wb,
                                        int4 *N, unsigned long long *qctr,
-                                       unsigned long long &n_dec) {
+                                       unsigned &n_dec) {
   bool d1[NE], d2[NE];
 #pragma unroll
   for (int i = 0; i < NE; i++) decide(a, v[i], e[i], p[i], ts, tn, d1[i], d2[i]);
@@ -280,7 +280,7 @@ __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bo
   for (int i = 0; i < NE; i++) {
     o1[i] = d1[i] ? atomicSub(&a.res[p[i].x], 1) : INT_MAX;
     o2[i] = d2[i] ? atomicSub(&a.res[p[i].y], 1) : INT_MAX;
-    n_dec += (unsigned long long)(d1[i] + d2[i]);
+    n_dec += (unsigned)(d1[i] + d2[i]);
   }
   // pending pushes of this lane, bit 2i (p[i].x) and 2i+1 (p[i].y); the
   // warp pushes one per lane per step through a single push_items site
@@ -310,8 +310,8 @@ template <int MINB, int G, bool OWN>
 __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   const int lane = lane_id();
   const int wib = threadIdx.x >> 5;
-  const int64_t gwarp = (int64_t)blockIdx.x * kWarps + wib;
-  const int64_t twarps = (int64_t)gridDim.x * kWarps;
+  const int gwarp = blockIdx.x * kWarps + wib;  // grids are one or two blocks per SM
+  const int twarps = gridDim.x * kWarps;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   PeelCtl *ctl = a.ctl;
   __shared__ int4 s_items[kWarps][kWQ];
@@ -330,11 +330,13 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   int4 *F = a.Q0, *N = a.Q1;
   int64_t nAlive = a.m;
   bool compact = false;  // rewrite the alive list during this scan
-  unsigned long long n_entries = 0, n_dec = 0, n_scan = 0;
+  // per-lane work counts (32-bit: a lane's share of even 2^33 list entries
+  // over the grid's 150 K lanes stays far below 2^32)
+  unsigned n_entries = 0, n_dec = 0, n_scan = 0;
   // this warp's first work items of the coming sub-round, loaded right after
   // the barrier together with the item count instead of after it
   int4 pre[G];
-  const int64_t it0 = gwarp * 4 * G + (lane >> 3);
+  const int64_t it0 = (int64_t)gwarp * 4 * G + (lane >> 3);
   auto prefetch = [&](const int4 *Q) {
 #pragma unroll
     for (int g = 0; g < G; g++)
@@ -377,7 +379,8 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
     // 4 x 32 entries per warp iteration: all loads are issued before any
     // decision, so one dependent round trip covers 4 entries per lane
     constexpr int kScanU = 4;
-    for (int64_t base = gwarp * 32 * kScanU; base < nAlive; base += twarps * 32 * kScanU) {
+    for (int64_t base = (int64_t)gwarp * 32 * kScanU; base < nAlive;
+         base += (int64_t)twarps * 32 * kScanU) {
       int e[kScanU], st[kScanU], r[kScanU];
 #pragma unroll
       for (int u = 0; u < kScanU; u++) {
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         ctl->qa[(ph + 1) % 3] = 0;
       }
       const int grp = lane >> 3, j = lane & 7;
-      for (int64_t base = gwarp * 4 * G; base < nCur; base += twarps * 4 * G) {
+      for (int64_t base = (int64_t)gwarp * 4 * G; base < nCur; base += (int64_t)twarps * 4 * G) {
         int ee[2 * G];
         bool vv[2 * G];
         int2 pp[2 * G];
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           la[g] = 0;
           lb[g] = 0;
           if (it < nCur) {
-            const int4 item = base == gwarp * 4 * G ? pre[g] : __ldcg(&F[it]);
+            const int4 item = base == (int64_t)gwarp * 4 * G ? pre[g] : __ldcg(&F[it]);
             const uint32_t hi = (uint32_t)item.y;
             ee[2 * g] = item.x;
             na[g] = OWN ? (int)(hi & 31u) : 0;
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         for (int g = 0; g < G; g++) {
           vv[2 * g] = vv[2 * g] && r[g] > 0;
           vv[2 * g + 1] = vv[2 * g + 1] && r[g] > 0;
-          n_entries += (unsigned long long)(vv[2 * g] + vv[2 * g + 1]);
+          n_entries += (unsigned)(vv[2 * g] + vv[2 * g + 1]);
         }
         charge<2 * G, OWN>(a, ee, vv, pp, k, ts, tn, wb, N, qn, n_dec);
       }
@@ -540,9 +543,9 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
     n_scan += __shfl_down_sync(TR_FULL, n_scan, o);
   }
   if (lane == 0) {
-    atomicAdd(&ctl->entries, n_entries);
-    atomicAdd(&ctl->decrements, n_dec);
-    atomicAdd(&ctl->scanned, n_scan);
+    atomicAdd(&ctl->entries, (unsigned long long)n_entries);
+    atomicAdd(&ctl->decrements, (unsigned long long)n_dec);
+    atomicAdd(&ctl->scanned, (unsigned long long)n_scan);
   }
 }
 
