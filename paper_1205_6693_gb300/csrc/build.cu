@@ -83,11 +83,23 @@ __global__ void k_lex_edges(int64_t rows, const uint64_t *sk, const int32_t *sro
   }
 }
 
+// U is sorted (edges in lexicographic order), so each run of equal tails
+// adds its length once: minus its first index at its first edge, its end at
+// its last (int32 wrap-around cancels).  Heads V are added once per group of
+// lanes of a warp that hold the same vertex.
 __global__ void k_degree(int64_t m, const int32_t *U, const int32_t *V, int32_t *deg) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    atomicAdd(&deg[U[e]], 1);
-    atomicAdd(&deg[V[e]], 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x; b < m; b += stride) {
+    const int64_t e = b + threadIdx.x;
+    const bool ok = e < m;
+    if (ok) {
+      const int u = U[e];
+      if (e == 0 || U[e - 1] != u) atomicAdd(&deg[u], -(int)e);
+      if (e + 1 == m || U[e + 1] != u) atomicAdd(&deg[u], (int)(e + 1));
+    }
+    const int v = ok ? V[e] : -1;
+    const unsigned peers = __match_any_sync(TR_FULL, v);
+    if (ok && lane_id() == __ffs(peers) - 1) atomicAdd(&deg[v], __popc(peers));
   }
 }
 
