@@ -215,8 +215,22 @@ typedef struct truss_run_stats {
   int32_t graphs;            /* 1, or G for a batch */
   /* stage times in ms (profile != 0), else 0 */
   float ms_build, ms_support, ms_lists, ms_peel, ms_scatter, ms_total;
-  /* algorithmic bytes (count_bytes != 0), else 0: see DESIGN notes in the
-   * library sources for the per-unit figures */
+  /* Algorithmic bytes of the three largest stages (count_bytes != 0, else
+   * 0).  bytes_support = 4 * sum over oriented edges (u, v) of
+   * (d+(u) + d+(v)) + 44 m + 24 T: the out-list entries a forward merge of
+   * each edge's two out-lists reads, its offsets, endpoints and support
+   * write, and three 8-byte read-modify-writes per triangle.  bytes_peel =
+   * sum over edges e = (u, v) of 12 min(L_u, L_v) + 12 (min(L_u, L_v) - 1)
+   * + 8, plus 16 T and 8 per edge present at each level that removes one:
+   * reading the alive neighbours of e's endpoint with fewer of them (id,
+   * edge id, state), looking each one up from the other endpoint, two
+   * read-modify-writes per destroyed triangle and the level scans; L_x is 1
+   * + the number of x's edges removed in a later sub-round than e (the
+   * fewest that any one-at-a-time removal order with the same sub-rounds
+   * leaves).
+   * bytes_lists = the list passes this library runs (8-byte records read
+   * twice, three list entries written, two cursor read-modify-writes per
+   * triangle, and the per-edge offsets and cursors). */
   double bytes_support, bytes_lists, bytes_peel;
   /* kernels this call launched (own kernels plus the CUB sort/scan passes) */
   int64_t launches;
@@ -231,6 +245,18 @@ typedef struct truss_run_stats {
   /* peel work (decompositions): triangle-list entries read, residual
    * decrements, alive-list entries scanned */
   int64_t peel_entries, peel_decrements, peel_scanned;
+  /* count_bytes != 0: the same two stages priced by the per-unit figures of
+   * the kernels this library runs (the support walk from each edge's middle
+   * vertex; the peel's list entries, partner states, decrements and alive-
+   * list entries), beside the formula figures above */
+  double design_bytes_support, design_bytes_peel;
+  /* count_bytes != 0: sum over edges of min(L_u, L_v) as above; the same
+   * with L_x counting every edge of x not removed before e's sub-round; sum
+   * over the levels that remove an edge of the edges present when they
+   * start; list entries the peel read whose triangle had already lost an
+   * edge, and those whose triangle lost it in an earlier level */
+  int64_t peel_sum_min_alive, peel_sum_min_alive_start, peel_alive_levels;
+  int64_t peel_dead_entries, peel_dead_earlier;
 } truss_run_stats;
 
 /* Statistics of the last successful call on this context. */
@@ -258,11 +284,15 @@ int truss_last_stats(truss_ctx *ctx, truss_run_stats *out);
  *
  * n must be <= TRUSS_NOALLOC_MAX_N and rows <= TRUSS_NOALLOC_MAX_ROWS;
  * anything larger is rejected with TRUSS_EINVAL before any device work.
- * src, dst and support_out must be device-accessible (device, managed or
- * mapped pinned memory); support_out[r] is the support of row r's edge, -1 for
- * a self-loop row.  The work runs on the current device on cuda_stream and the
- * call waits for it (it reads back one status word).  Errors: TRUSS_EINVAL
- * (sizes, null or host-only pointers, a vertex id outside [0, n)),
+ * src, dst and support_out must be reachable by a kernel on the current
+ * device as given: memory of the current device, managed memory, or pinned
+ * host memory mapped at the same address.  Memory of another GPU and pageable
+ * host memory are refused with TRUSS_EINVAL before any launch.
+ * support_out[r] is the support of row r's edge, -1 for a self-loop row.  The
+ * work runs on the current device on cuda_stream and the call waits for it
+ * (it reads back one status word).  Errors: TRUSS_EINVAL (sizes, null
+ * pointers, pointers the current device cannot use as given, a vertex id
+ * outside [0, n)),
  * TRUSS_ECUDA. */
 int truss_support_noalloc(int64_t n, int64_t rows, const int32_t *src, const int32_t *dst,
                           int32_t *support_out, void *cuda_stream);
@@ -282,7 +312,7 @@ int truss_support_noalloc(int64_t n, int64_t rows, const int32_t *src, const int
 typedef struct truss_server truss_server;
 
 typedef struct truss_serve_opts {
-  int64_t hbm_budget_bytes; /* 0 = half of the device memory free at start */
+  int64_t hbm_budget_bytes; /* 0 = a third of the device memory free at start */
   int32_t max_inflight;     /* admitted, unfinished requests (0 = 256) */
   int32_t streams;          /* worker threads / streams (0 = 4) */
   int64_t batch_rows;       /* requests with <= this many rows are batched (0 = 65536) */
@@ -309,13 +339,20 @@ typedef struct truss_serve_stats {
   double wall_s;            /* first submit -> last completion */
   double edges_per_s;       /* edges / wall_s */
   int64_t launches;         /* single + batched decompositions run */
+  int64_t retried;          /* requests run again alone after exceeding their run's cap */
 } truss_serve_stats;
 
 /* Projected device footprint (bytes) used for admission of a request of
  * `rows` rows over `n` vertices: 96 bytes per row for the edge keys, CSR,
  * supports and peel queues, 16 per vertex, and 8-byte triangle-list entries
  * for an assumed 3 x 32 triangle incidences per row (the exact figure is
- * known only after the support pass). */
+ * known only after the support pass).  A run's workspace is capped at twice
+ * the projection of its requests; a request that needs more (a graph much
+ * denser in triangles than assumed) fails that run with TRUSS_ENOMEM, is
+ * queued again once at the head of the queue with the whole budget as its
+ * footprint, and then runs alone with the whole budget as its cap: it
+ * completes, or fails alone with TRUSS_ENOMEM, and no other request loses
+ * memory to it. */
 int64_t truss_serve_footprint(int64_t n, int64_t rows);
 
 /* Start a server on ctx's device with ctx's options (ctx itself is not used

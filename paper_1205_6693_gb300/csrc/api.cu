@@ -55,10 +55,19 @@ Arena::~Arena() { release_all(); }
 void Arena::release_all() {
   for (auto &c : chunks_) cudaFree(c.p);
   chunks_.clear();
+  handed_ = 0;
 }
 
 void Arena::reset() {
   for (auto &c : chunks_) c.used = 0;
+  handed_ = 0;
+}
+
+size_t Arena::headroom(size_t free_dev) const {
+  const size_t room = unused() + free_dev;
+  if (!limit_) return room;
+  const size_t left = limit_ > handed_ ? limit_ - handed_ : 0;
+  return left < room ? left : room;
 }
 
 size_t Arena::unused() const {
@@ -80,16 +89,22 @@ std::vector<size_t> Arena::mark() const {
 }
 
 void Arena::rewind(const std::vector<size_t> &m) {
-  for (size_t i = 0; i < chunks_.size(); i++) chunks_[i].used = i < m.size() ? m[i] : 0;
+  handed_ = 0;
+  for (size_t i = 0; i < chunks_.size(); i++) {
+    chunks_[i].used = i < m.size() ? m[i] : 0;
+    handed_ += chunks_[i].used;
+  }
 }
 
 void *Arena::alloc(size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
   if (bytes == 0) bytes = 256;
+  if (limit_ && handed_ + bytes > limit_) return nullptr;
   for (auto &c : chunks_) {
     if (c.cap - c.used >= bytes) {
       void *p = c.p + c.used;
       c.used += bytes;
+      handed_ += bytes;
       return p;
     }
   }
@@ -100,6 +115,7 @@ void *Arena::alloc(size_t bytes) {
     return nullptr;
   }
   chunks_.push_back(Chunk{p, cap, bytes});
+  handed_ += bytes;
   return p;
 }
 
@@ -333,6 +349,7 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
     tr::PeelCfg pcfg;
     pcfg.sms = ctx->sms;
     pcfg.variant = ctx->opts.peel_variant;
+    pcfg.count = ctx->opts.count_bytes != 0 && !tids;
     if (ctx->opts.wait_limit_ns > 0) pcfg.wait_ns = ctx->opts.wait_limit_ns;
     int rc = tids ? tr::run_peel_async(A, g, so, pairs, tids, so.records, pcfg, truss_e, &pr, s)
                   : tr::run_peel(A, g, so, lists, pcfg, truss_e, &pr, s);
@@ -385,14 +402,25 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   }
   st.launches = tr::take_launches();
   if (ctx->opts.count_bytes) {
-    double bs = 0, bl = 0;
-    TR_TRY(tr::count_support_bytes(A, g, st.triangles, so.tb != nullptr, so.in_place, &bs, &bl,
-                                   s));
+    double bs = 0, bsd = 0, bl = 0;
+    TR_TRY(tr::count_support_bytes(A, g, st.triangles, so.tb != nullptr, so.in_place, &bs, &bsd,
+                                   &bl, s));
     st.bytes_support = bs;
+    st.design_bytes_support = bsd;
     st.bytes_lists = want_truss ? bl : 0.0;
-    if (want_truss)
-      st.bytes_peel = (so.in_place ? 40.0 : 28.0) * (double)g.m + 16.0 * (double)pr.entries +
-                      8.0 * (double)pr.decrements + 16.0 * (double)pr.scanned;
+    if (want_truss) {
+      st.design_bytes_peel = (so.in_place ? 40.0 : 28.0) * (double)g.m +
+                             16.0 * (double)pr.entries + 8.0 * (double)pr.decrements +
+                             16.0 * (double)pr.scanned;
+      const double smin = (double)pr.sum_min_alive;
+      st.bytes_peel = 12.0 * smin + 12.0 * (smin - (double)g.m) + 8.0 * (double)g.m +
+                      16.0 * (double)st.triangles + 8.0 * (double)pr.alive_levels;
+      st.peel_sum_min_alive = (int64_t)pr.sum_min_alive;
+      st.peel_sum_min_alive_start = (int64_t)pr.sum_min_alive_start;
+      st.peel_alive_levels = (int64_t)pr.alive_levels;
+      st.peel_dead_entries = (int64_t)pr.dead;
+      st.peel_dead_earlier = (int64_t)pr.dead_earlier;
+    }
   }
   ctx->last = st;
   return TRUSS_OK;
@@ -886,6 +914,7 @@ void ctx_trim(truss_ctx *ctx, size_t max_bytes) {
   }
 }
 const truss_opts *ctx_opts(truss_ctx *ctx) { return &ctx->opts; }
+void ctx_set_limit(truss_ctx *ctx, size_t bytes) { ctx->arena.set_limit(bytes); }
 }  // namespace tr
 
 extern "C" {

@@ -36,6 +36,15 @@ int sort_pairs_u64(void *tmp, size_t *tmp_bytes, const uint64_t *kin, uint64_t *
                "SortPairs<u64>");
 }
 
+int sort_keys_u64(void *tmp, size_t *tmp_bytes, const uint64_t *kin, uint64_t *kout, int64_t n,
+                  int begin_bit, int end_bit, cudaStream_t s) {
+  if (n > INT32_MAX) return TRUSS_EINVAL;
+  if (tmp) count_launches(sort_launches(n, end_bit - begin_bit));
+  return check(cub::DeviceRadixSort::SortKeys(tmp, *tmp_bytes, kin, kout, (int)n, begin_bit,
+                                              end_bit, s),
+               "SortKeys<u64>");
+}
+
 int sort_pairs_u32(void *tmp, size_t *tmp_bytes, const uint32_t *kin, uint32_t *kout,
                    const int32_t *vin, int32_t *vout, int64_t n, int begin_bit, int end_bit,
                    cudaStream_t s) {

@@ -30,6 +30,13 @@ class Arena {
   }
   size_t reserved() const;
   size_t unused() const;  // bytes of reserved chunks not handed out since reset()
+  // Cap on the bytes handed out since reset() (0 = none): alloc() returns
+  // nullptr rather than exceed it.
+  void set_limit(size_t bytes) { limit_ = bytes; }
+  // Bytes alloc() can still hand out, given `free_dev` bytes of free device
+  // memory: what the cap leaves, and no more than the reserved chunks' spare
+  // room plus free_dev.
+  size_t headroom(size_t free_dev) const;
   void release_all();
   // Allocation state, to hand back everything allocated after it (rewind);
   // chunks reserved since stay reserved.
@@ -42,6 +49,8 @@ class Arena {
     size_t cap, used;
   };
   std::vector<Chunk> chunks_;
+  size_t limit_ = 0;
+  size_t handed_ = 0;  // bytes handed out since reset()
 };
 
 // ------------------------------------------------------------ CUB glue ---
@@ -50,6 +59,8 @@ class Arena {
 int sort_pairs_u64(void *tmp, size_t *tmp_bytes, const uint64_t *kin, uint64_t *kout,
                    const int32_t *vin, int32_t *vout, int64_t n, int begin_bit, int end_bit,
                    cudaStream_t s);
+int sort_keys_u64(void *tmp, size_t *tmp_bytes, const uint64_t *kin, uint64_t *kout, int64_t n,
+                  int begin_bit, int end_bit, cudaStream_t s);
 int sort_pairs_u32(void *tmp, size_t *tmp_bytes, const uint32_t *kin, uint32_t *kout,
                    const int32_t *vin, int32_t *vout, int64_t n, int begin_bit, int end_bit,
                    cudaStream_t s);
@@ -155,11 +166,26 @@ struct PeelCfg {
   // last level to run (0 = all).  Edges not removed by then get truss 0.
   const uint8_t *pinned = nullptr;
   int k_stop = 0;
+  // Counting run (untimed): record each edge's removal sub-round and the
+  // per-level list-entry counts, and compute the algorithmic bytes of the
+  // removals (PeelResult::sum_min_alive .. alive_levels).
+  bool count = false;
 };
 
 struct PeelResult {
   int32_t kmax = 0, levels = 0, subrounds = 0, err = 0;
   unsigned long long entries = 0, decrements = 0, scanned = 0;
+  // counting runs only:
+  //  sum_min_alive = sum over edges e = (u, v) of min(L_u, L_v), L_x = 1 +
+  //    the number of x's edges removed in a later sub-round than e (e last
+  //    among the edges its sub-round removes); sum_min_alive_start counts
+  //    in L_x every edge of x not removed before e's sub-round;
+  //  alive_levels = sum over the levels k that remove an edge of the edges
+  //    present when level k starts;
+  //  dead = list entries read whose triangle had already lost an edge,
+  //    dead_earlier = those whose triangle lost it in an earlier level.
+  unsigned long long sum_min_alive = 0, sum_min_alive_start = 0, alive_levels = 0, dead = 0,
+                     dead_earlier = 0;
 };
 
 // Barrier-free peel (peel_async.cu): needs the list entries' triangle ids
@@ -169,6 +195,10 @@ int run_peel_async(Arena &A, const Csr &g, const SupportOut &so, const int2 *pai
                    PeelResult *out, cudaStream_t s);
 int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, const PeelCfg &cfg,
              int32_t *truss, PeelResult *res, cudaStream_t s);
+// sum[0] = sum_min_alive, sum[1] = sum_min_alive_start (see PeelResult) from
+// each edge's removal sub-round `when` (peel.cu).
+int count_min_alive(Arena &A, const Csr &g, const SupportOut &so, const int32_t *when,
+                    unsigned long long *sum, cudaStream_t s);
 
 // -------------------------------------------------------------- outputs ---
 int scatter_rows(const Csr &g, const int32_t *sup, const int32_t *truss, int32_t *sup_rows,
@@ -229,7 +259,13 @@ int pin_edges(int64_t rows, const int32_t *row2e, const uint8_t *pinned_rows, ui
 int run_core(Arena &A, const Csr &g, int sms, long long wait_ns, int32_t *core_out,
              int32_t *kmax, int32_t *levels, int32_t *subrounds, cudaStream_t s);
 
+// Algorithmic bytes of the support pass: b_sup by the per-edge formula
+// 4 * sum over oriented edges (u, v) of (d+(u) + d+(v)) + 44 m + 24 T (a
+// forward merge of the two out-lists of every edge, its offsets, endpoints,
+// support write and the three read-modify-writes per triangle); b_sup_design
+// by the per-unit figures of the walk this library runs (support.cu); b_lists
+// of the list passes.
 int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, bool in_place,
-                        double *b_sup, double *b_lists, cudaStream_t s);
+                        double *b_sup, double *b_sup_design, double *b_lists, cudaStream_t s);
 
 }  // namespace tr

@@ -211,14 +211,22 @@ int scratch_for_current_device(unsigned char **out) {
   return TRUSS_OK;
 }
 
-bool device_accessible(const void *p) {
+// True if the kernel, launched on device `dev`, may dereference p as given:
+// memory of that same device, managed memory, or pinned host memory mapped
+// at the same address.  Memory of another GPU is refused (without peer
+// access a kernel reading it would fault), and so is pageable host memory.
+bool device_accessible(const void *p, int dev) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
-         (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr);
+  switch (at.type) {
+    case cudaMemoryTypeDevice: return at.device == dev;
+    case cudaMemoryTypeManaged: return true;
+    case cudaMemoryTypeHost: return at.devicePointer == p;
+    default: return false;
+  }
 }
 
 }  // namespace
@@ -229,7 +237,13 @@ extern "C" int truss_support_noalloc(int64_t n, int64_t rows, const int32_t *src
   if (n < 0 || rows < 0 || n > kMaxN || rows > kMaxRows) return TRUSS_EINVAL;
   if (rows == 0) return TRUSS_OK;
   if (!src || !dst || !support_out || n == 0) return TRUSS_EINVAL;
-  if (!device_accessible(src) || !device_accessible(dst) || !device_accessible(support_out))
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TRUSS_ECUDA;
+  }
+  if (!device_accessible(src, dev) || !device_accessible(dst, dev) ||
+      !device_accessible(support_out, dev))
     return TRUSS_EINVAL;
   unsigned char *scratch = nullptr;
   TR_TRY(scratch_for_current_device(&scratch));

@@ -81,6 +81,7 @@ struct PeelCtl {
   int live[3];               // alive edges left after each scan
   int levels, subrounds, kmax, ntrace;
   unsigned long long entries, decrements, scanned;
+  unsigned long long dead, dead_earlier;  // counting runs
 };
 
 struct PeelArgs {
@@ -104,6 +105,12 @@ struct PeelArgs {
   PeelCtl *ctl;
   long long wait_ns;
   int k_stop;  // last level to run (0 = all)
+  // counting runs (the COUNT kernel): removal sub-round of every edge, and
+  // per level k < lvl_cap the entries read, those of destroyed triangles, and
+  // those of triangles destroyed in an earlier level (lvl[3k .. 3k+2])
+  int32_t *when;
+  unsigned long long *lvl;
+  int lvl_cap;
 };
 
 __device__ __forceinline__ int items_of(int len) { return len > 0 ? (len + kItem - 1) / kItem : 1; }
@@ -240,8 +247,8 @@ __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, 
 // them.  d1 / d2 = decrement p1 / p2 (the partners not in the frontier).
 // ts / tn = tag(s) / tag(s+1).
 __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int2 pr, int ts,
-                                       int tn, bool &d1, bool &d2) {
-  d1 = d2 = false;
+                                       int tn, bool &d1, bool &d2, bool &dead) {
+  d1 = d2 = dead = false;
   if (!valid) return;
   const int p1 = pr.x, p2 = pr.y;
   if ((uint32_t)p1 >= (uint32_t)a.m || (uint32_t)p2 >= (uint32_t)a.m) {
@@ -250,7 +257,8 @@ __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int
   }
   const int s1 = __ldcg(&a.stamp[p1]), s2 = __ldcg(&a.stamp[p2]);
   const bool dead1 = s1 != 0 && s1 != ts && s1 != tn, dead2 = s2 != 0 && s2 != ts && s2 != tn;
-  if (dead1 || dead2) return;
+  dead = dead1 || dead2;
+  if (dead) return;
   const bool in1 = s1 == ts, in2 = s2 == ts;
   if (!in1 && !in2) {
     d1 = true;
@@ -267,14 +275,26 @@ __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int
 // decrements its partners outside the frontier; a partner whose residual
 // crosses k-1 -> k-2 joins the next frontier.  All loads and atomics of the
 // NE entries are issued before any result is used.
-template <int NE, bool OWN>
+template <int NE, bool OWN, bool COUNT>
 __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bool *v,
                                        const int2 *p, int k, int ts, int tn, WarpBuf &wb,
                                        int4 *N, unsigned long long *qctr,
-                                       unsigned &n_dec) {
-  bool d1[NE], d2[NE];
+                                       unsigned &n_dec, int s_lvl0, unsigned &n_dead,
+                                       unsigned &n_early) {
+  bool d1[NE], d2[NE], dd[NE];
 #pragma unroll
-  for (int i = 0; i < NE; i++) decide(a, v[i], e[i], p[i], ts, tn, d1[i], d2[i]);
+  for (int i = 0; i < NE; i++) decide(a, v[i], e[i], p[i], ts, tn, d1[i], d2[i], dd[i]);
+  if (COUNT) {
+    // a destroyed triangle lost its first edge when the earlier-removed of
+    // its removed partners went (partners still alive have no removal yet)
+#pragma unroll
+    for (int i = 0; i < NE; i++) {
+      if (!dd[i]) continue;
+      const int w1 = __ldcg(&a.when[p[i].x]), w2 = __ldcg(&a.when[p[i].y]);
+      n_dead++;
+      n_early += min(w1, w2) < s_lvl0;
+    }
+  }
   int o1[NE], o2[NE];
 #pragma unroll
   for (int i = 0; i < NE; i++) {
@@ -306,7 +326,7 @@ __device__ __forceinline__ void charge(const PeelArgs &a, const int *e, const bo
 // 128 registers per thread, 2: 64); G = work items per 8-lane group per
 // iteration (2 entries per lane per item).
 // OWN: the lists keep own parts in the records (TriLists::own_cnt set).
-template <int MINB, int G, bool OWN>
+template <int MINB, int G, bool OWN, bool COUNT = false>
 __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   const int lane = lane_id();
   const int wib = threadIdx.x >> 5;
@@ -333,6 +353,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   // per-lane work counts (32-bit: a lane's share of even 2^33 list entries
   // over the grid's 150 K lanes stays far below 2^32)
   unsigned n_entries = 0, n_dec = 0, n_scan = 0;
+  unsigned n_dead = 0, n_early = 0;  // counting runs: totals so far
   // this warp's first work items of the coming sub-round, loaded right after
   // the barrier together with the item count instead of after it
   int4 pre[G];
@@ -451,7 +472,9 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
     }
     // --------------------------------------------------------- sub-rounds ---
     int64_t nCur = nF;
+    const int s_lvl0 = s;  // first sub-round of this level
     for (;;) {
+      const unsigned c_ent = n_entries, c_dead = n_dead, c_early = n_early;
       if (!retag()) return;
       const int ts = tag_of(s), tn = tag_of(s + 1);
       if (leader && a.trace && ctl->ntrace < a.trace_cap) {
@@ -487,7 +510,10 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
             cnt[g] = na[g] + ((hi >> 5) & 31u);
             la[g] = OWN ? (int64_t)(((uint64_t)((hi >> 11) & 0x3FFu) << 32) | (uint32_t)item.z) : 0;
             lb[g] = (int64_t)(((uint64_t)(hi >> 21) << 32) | (uint32_t)item.w);
-            if (((hi >> 10) & 1u) && j == 0) a.truss[item.x] = k;
+            if (((hi >> 10) & 1u) && j == 0) {
+              a.truss[item.x] = k;
+              if (COUNT) a.when[item.x] = s;
+            }
           }
           ee[2 * g + 1] = ee[2 * g];
         }
@@ -512,9 +538,23 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           vv[2 * g + 1] = vv[2 * g + 1] && r[g] > 0;
           n_entries += (unsigned)(vv[2 * g] + vv[2 * g + 1]);
         }
-        charge<2 * G, OWN>(a, ee, vv, pp, k, ts, tn, wb, N, qn, n_dec);
+        charge<2 * G, OWN, COUNT>(a, ee, vv, pp, k, ts, tn, wb, N, qn, n_dec, s_lvl0, n_dead,
+                                  n_early);
       }
       flush_items(a, wb, N, qn);
+      if (COUNT && k < a.lvl_cap) {
+        unsigned x0 = n_entries - c_ent, x1 = n_dead - c_dead, x2 = n_early - c_early;
+        for (int o = 16; o >= 1; o >>= 1) {
+          x0 += __shfl_down_sync(TR_FULL, x0, o);
+          x1 += __shfl_down_sync(TR_FULL, x1, o);
+          x2 += __shfl_down_sync(TR_FULL, x2, o);
+        }
+        if (lane == 0 && (x0 | x1 | x2)) {
+          atomicAdd(&a.lvl[3 * k], (unsigned long long)x0);
+          atomicAdd(&a.lvl[3 * k + 1], (unsigned long long)x1);
+          atomicAdd(&a.lvl[3 * k + 2], (unsigned long long)x2);
+        }
+      }
       if (!grid_barrier(&ctl->bar, &ctl->err, a.wait_ns)) return;
       ph++;
       prefetch(N);
@@ -541,11 +581,19 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
     n_entries += __shfl_down_sync(TR_FULL, n_entries, o);
     n_dec += __shfl_down_sync(TR_FULL, n_dec, o);
     n_scan += __shfl_down_sync(TR_FULL, n_scan, o);
+    if (COUNT) {
+      n_dead += __shfl_down_sync(TR_FULL, n_dead, o);
+      n_early += __shfl_down_sync(TR_FULL, n_early, o);
+    }
   }
   if (lane == 0) {
     atomicAdd(&ctl->entries, (unsigned long long)n_entries);
     atomicAdd(&ctl->decrements, (unsigned long long)n_dec);
     atomicAdd(&ctl->scanned, (unsigned long long)n_scan);
+    if (COUNT) {
+      atomicAdd(&ctl->dead, (unsigned long long)n_dead);
+      atomicAdd(&ctl->dead_earlier, (unsigned long long)n_early);
+    }
   }
 }
 
@@ -570,7 +618,148 @@ __global__ void k_peel_init(int64_t m, const int32_t *sup, const uint8_t *pinned
   }
 }
 
+// Removal-order figures of a counting run (PeelResult): min alive degrees
+// from the removal sub-rounds, the edges present at each level that removes
+// one (from the truss-number histogram), and the per-level entry counts,
+// written to the file named by TRUSS_LEVEL_STATS if set.
+__global__ void k_truss_hist(int64_t m, const int32_t *truss, int cap,
+                             unsigned long long *cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = truss[e];
+    if (k >= 0 && k < cap) atomicAdd(&cnt[k], 1ull);
+  }
+}
+
+int count_run(Arena &A, const Csr &g, const SupportOut &so, const PeelArgs &a, const PeelCtl &h,
+              const int32_t *truss, PeelResult *out, cudaStream_t s) {
+  const int cap = h.kmax + 2 < a.lvl_cap ? h.kmax + 2 : a.lvl_cap;
+  unsigned long long *cnt = A.get<unsigned long long>(cap);
+  if (!cnt) return TRUSS_ENOMEM;
+  TR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * cap, s));
+  k_truss_hist<<<grid_for(g.m, 256, 152 * 16), 256, 0, s>>>(g.m, truss, cap, cnt);
+  TR_LAUNCHED();
+  std::vector<unsigned long long> hc((size_t)cap), hl((size_t)3 * cap);
+  TR_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * cap,
+                          cudaMemcpyDeviceToHost, s));
+  TR_CUDA(cudaMemcpyAsync(hl.data(), a.lvl, sizeof(unsigned long long) * 3 * cap,
+                          cudaMemcpyDeviceToHost, s));
+  unsigned long long sums[2] = {0, 0};
+  TR_TRY(count_min_alive(A, g, so, a.when, sums, s));
+  TR_CUDA(cudaStreamSynchronize(s));
+  // edges present when level k starts: truss number >= k
+  std::vector<unsigned long long> alive((size_t)cap + 1, 0);
+  for (int k = cap - 1; k >= 0; k--) alive[k] = alive[k + 1] + hc[k];
+  out->alive_levels = 0;
+  for (int k = 0; k < cap; k++)
+    if (hc[k] > 0) out->alive_levels += alive[k];
+  out->sum_min_alive = sums[0];
+  out->sum_min_alive_start = sums[1];
+  out->dead = h.dead;
+  out->dead_earlier = h.dead_earlier;
+  if (const char *path = getenv("TRUSS_LEVEL_STATS")) {
+    if (FILE *f = fopen(path, "w")) {
+      fprintf(f, "k,removed,present,entries,dead,dead_earlier\n");
+      for (int k = 0; k < cap; k++)
+        if (hc[k] > 0 || hl[3 * k] > 0)
+          fprintf(f, "%d,%llu,%llu,%llu,%llu,%llu\n", k, hc[k], alive[k], hl[3 * k],
+                  hl[3 * k + 1], hl[3 * k + 2]);
+      fclose(f);
+    }
+  }
+  return TRUSS_OK;
+}
+
+// Keys (endpoint, removal sub-round) of both endpoints of every edge.
+__global__ void k_when_keys(int64_t m, const int32_t *esrc, const int32_t *adjp,
+                            const int32_t *when, uint64_t *keys) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t w = (uint32_t)when[e];
+    keys[2 * e] = (uint64_t)(uint32_t)esrc[e] << 32 | w;
+    keys[2 * e + 1] = (uint64_t)(uint32_t)adjp[e] << 32 | w;
+  }
+}
+
+// Degree of every vertex (out-edges + in-edges); entry n is 0.
+__global__ void k_sym_degree(int64_t n, const int64_t *offp, const int64_t *inoff,
+                             int64_t *deg) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u <= n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    deg[u] = u < n ? (offp[u + 1] - offp[u]) + (inoff[u + 1] - inoff[u]) : 0;
+}
+
+// Entries of the sorted run keys[lo, hi) that are >= key.
+__device__ __forceinline__ int64_t count_ge(const uint64_t *keys, int64_t lo, int64_t hi,
+                                            uint64_t key) {
+  const int64_t end = hi;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (keys[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return end - lo;
+}
+
+// acc[0] += min over e's endpoints x of (1 + x's edges removed in a later
+// sub-round than e); acc[1] += the same with every edge not removed before
+// e's sub-round (e's co-frontier edges included).
+__global__ void k_min_alive(int64_t m, const int32_t *esrc, const int32_t *adjp,
+                            const int32_t *when, const int64_t *soff, const uint64_t *keys,
+                            unsigned long long *acc) {
+  unsigned long long lo = 0, hi = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int u = esrc[e], v = adjp[e];
+    const uint64_t w = (uint32_t)when[e];
+    const uint64_t ku = (uint64_t)(uint32_t)u << 32 | w, kv = (uint64_t)(uint32_t)v << 32 | w;
+    const int64_t su = count_ge(keys, soff[u], soff[u + 1], ku);
+    const int64_t sv = count_ge(keys, soff[v], soff[v + 1], kv);
+    const int64_t au = 1 + count_ge(keys, soff[u], soff[u + 1], ku + 1);
+    const int64_t av = 1 + count_ge(keys, soff[v], soff[v + 1], kv + 1);
+    hi += (unsigned long long)(su < sv ? su : sv);
+    lo += (unsigned long long)(au < av ? au : av);
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    lo += __shfl_down_sync(TR_FULL, lo, o);
+    hi += __shfl_down_sync(TR_FULL, hi, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (lo) atomicAdd(&acc[0], lo);
+    if (hi) atomicAdd(&acc[1], hi);
+  }
+}
+
 }  // namespace
+
+int count_min_alive(Arena &A, const Csr &g, const SupportOut &so, const int32_t *when,
+                    unsigned long long *sum, cudaStream_t s) {
+  const int64_t m = g.m, n = g.n;
+  sum[0] = sum[1] = 0;
+  if (m == 0) return TRUSS_OK;
+  if (!so.inoff) return TRUSS_EINVAL;
+  uint64_t *k0 = A.get<uint64_t>(2 * m), *k1 = A.get<uint64_t>(2 * m);
+  int64_t *deg = A.get<int64_t>(n + 1), *soff = A.get<int64_t>(n + 1);
+  unsigned long long *acc = A.get<unsigned long long>(2);
+  if (!k0 || !k1 || !deg || !soff || !acc) return TRUSS_ENOMEM;
+  k_when_keys<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, g.esrc, g.adjp, when, k0);
+  TR_LAUNCHED();
+  k_sym_degree<<<grid_for(n + 1, 256, 152 * 16), 256, 0, s>>>(n, g.offp, so.inoff, deg);
+  TR_LAUNCHED();
+  const int end_bit = 32 + bits_for((uint64_t)(n > 0 ? n - 1 : 0));
+  size_t tb = 0, tb2 = 0;
+  TR_TRY(sort_keys_u64(nullptr, &tb, k0, k1, 2 * m, 0, end_bit, s));
+  TR_TRY(exclusive_sum_i64(nullptr, &tb2, deg, soff, n + 1, s));
+  void *tmp = A.alloc(tb > tb2 ? tb : tb2);
+  if (!tmp) return TRUSS_ENOMEM;
+  TR_TRY(sort_keys_u64(tmp, &tb, k0, k1, 2 * m, 0, end_bit, s));
+  TR_TRY(exclusive_sum_i64(tmp, &tb2, deg, soff, n + 1, s));
+  TR_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), s));
+  k_min_alive<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, g.esrc, g.adjp, when, soff, k1, acc);
+  TR_LAUNCHED();
+  TR_CUDA(cudaMemcpyAsync(sum, acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  TR_CUDA(cudaStreamSynchronize(s));
+  return TRUSS_OK;
+}
 
 int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, const PeelCfg &cfg,
              int32_t *truss, PeelResult *out, cudaStream_t s) {
@@ -603,7 +792,9 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, co
   const int variant = cfg.variant == 1 ? 1 : (cfg.variant == 3 ? 3 : 2);
   const bool own = L.own_cnt != nullptr;
   const void *kern;
-  if (own) {
+  if (cfg.count) {
+    kern = own ? (const void *)k_peel<2, 1, true, true> : (const void *)k_peel<2, 1, false, true>;
+  } else if (own) {
     kern = variant == 1   ? (const void *)k_peel<1, 2, true>
            : variant == 3 ? (const void *)k_peel<1, 1, true>
                           : (const void *)k_peel<2, 1, true>;
@@ -615,7 +806,7 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, co
   int occ = 0;
   TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPeelBlock, 0));
   if (occ < 1) return TRUSS_ECUDA;
-  if (variant != 2 && occ > 1) occ = 1;
+  if (variant != 2 && !cfg.count && occ > 1) occ = 1;
   PeelArgs a{};
   a.m = m;
   a.sup = so.sup;
@@ -640,6 +831,15 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, co
   a.ctl = ctl;
   a.wait_ns = cfg.wait_ns;
   a.k_stop = cfg.k_stop;
+  constexpr int kLvlCap = 1 << 16;
+  if (cfg.count) {
+    a.when = A.get<int32_t>(m);
+    a.lvl = A.get<unsigned long long>(3 * (int64_t)kLvlCap);
+    if (!a.when || !a.lvl) return TRUSS_ENOMEM;
+    a.lvl_cap = kLvlCap;
+    TR_CUDA(cudaMemsetAsync(a.when, 0x7F, sizeof(int32_t) * m, s));  // never removed
+    TR_CUDA(cudaMemsetAsync(a.lvl, 0, sizeof(unsigned long long) * 3 * kLvlCap, s));
+  }
   const char *trace_path = getenv("TRUSS_TRACE");
   const int trace_cap = 1 << 20;
   if (trace_path) {
@@ -672,6 +872,7 @@ int run_peel(Arena &A, const Csr &g, const SupportOut &so, const TriLists &L, co
     }
   }
   if (h.err != 0) return h.err;
+  if (cfg.count) TR_TRY(count_run(A, g, so, a, h, truss, out, s));
   return TRUSS_OK;
 }
 

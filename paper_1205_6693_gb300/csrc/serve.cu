@@ -12,6 +12,15 @@
 // device through their separate streams.  Each request's result is exactly
 // that of a decomposition of the request alone (truss numbers of a disjoint
 // union are those of its components, Definition 2).
+//
+// The projection behind admission cannot know a graph's triangle count, so
+// each run's workspace is capped at twice the projected footprint of its
+// requests (the context's arena refuses to hand out more; the pipeline
+// first falls back to its lower-memory list layouts).  A run that still
+// needs more fails with TRUSS_ENOMEM without taking memory from the others;
+// its requests are then queued again at the head, once each, with the whole
+// budget as their footprint, so each runs alone with the whole budget as its
+// cap and either completes or fails alone.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -33,6 +42,7 @@ int decompose_batch_counts(truss_ctx *ctx, int32_t G, const int64_t *n, const in
 int ctx_device(truss_ctx *ctx);
 const truss_opts *ctx_opts(truss_ctx *ctx);
 void ctx_trim(truss_ctx *ctx, size_t max_bytes);
+void ctx_set_limit(truss_ctx *ctx, size_t bytes);
 }  // namespace tr
 
 namespace {
@@ -50,6 +60,7 @@ struct Request {
   int64_t fp = 0;
   Clock::time_point t_submit, t_start, t_done;
   bool done = false;
+  bool retried = false;  // queued again after a run that ran out of its cap
   int rc = TRUSS_OK;
   std::vector<int32_t> sup, tr;
   truss_req_stats st{};
@@ -72,6 +83,7 @@ struct truss_server {
   uint64_t next_id = 1;
   // statistics
   int64_t submitted = 0, admitted = 0, rejected = 0, completed = 0, failed = 0, edges = 0;
+  int64_t retried = 0;
   int64_t launches = 0;
   std::vector<double> lat_ms;
   Clock::time_point first_submit, last_done;
@@ -202,6 +214,11 @@ void worker_main(truss_server *S) {
       S->launches++;
     }
     if (rc == TRUSS_OK) {
+      // workspace cap of this run: twice the projection, or the whole budget
+      // for a request queued again after running out of its cap
+      size_t cap = 0;
+      for (Request *r : job) cap += (size_t)(r->retried ? r->fp : 2 * r->fp);
+      tr::ctx_set_limit(ctx, cap);
       run_job(ctx, st, job, &dsrc, &ddst, &dcap);
       // keep the cached workspace within this worker's share of the budget
       tr::ctx_trim(ctx, (size_t)(S->o.hbm_budget_bytes / S->o.streams));
@@ -215,9 +232,18 @@ void worker_main(truss_server *S) {
     {
       std::lock_guard<std::mutex> lk(S->mu);
       for (Request *r : job) {
-        r->done = true;
         S->inflight--;
         S->inflight_fp -= r->fp;
+        if (r->rc == TRUSS_ENOMEM && !r->retried) {
+          r->retried = true;
+          r->fp = S->o.hbm_budget_bytes;  // admitted only when nothing else runs
+          r->rc = TRUSS_OK;
+          S->retried++;
+          S->admitted--;  // counted again when it is admitted alone
+          S->pending.push_front(r);
+          continue;
+        }
+        r->done = true;
         if (r->rc == TRUSS_OK) {
           S->completed++;
           S->edges += r->st.m;
@@ -282,7 +308,9 @@ int truss_serve_start(truss_ctx *ctx, const truss_serve_opts *opts, truss_server
       delete S;
       return TRUSS_ECUDA;
     }
-    S->o.hbm_budget_bytes = (int64_t)(fr / 2);
+    // runs use at most twice their projection, plus the workspace each
+    // worker keeps cached between runs (at most budget / streams)
+    S->o.hbm_budget_bytes = (int64_t)(fr / 3);
   }
   try {
     for (int i = 0; i < S->o.streams; i++) S->workers.emplace_back(worker_main, S);
@@ -382,6 +410,7 @@ int truss_serve_stop(truss_server *S, truss_serve_stats *st) {
     o.failed = S->failed;
     o.edges = S->edges;
     o.launches = S->launches;
+    o.retried = S->retried;
     std::vector<double> l = S->lat_ms;
     std::sort(l.begin(), l.end());
     if (!l.empty()) {

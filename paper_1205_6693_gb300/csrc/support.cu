@@ -805,7 +805,7 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
       cudaGetLastError();
       fr = 0;
     }
-    const double avail = (double)fr + (double)A.unused();
+    const double avail = (double)A.headroom(fr);
     const double need_whole = 1.05 * (32.0 * (double)R + 20.0 * (double)m);
     const double need_in_place = 1.05 * (24.0 * (double)R + 36.0 * (double)m);
     bool use = false;
@@ -1006,16 +1006,39 @@ __global__ void k_count_list_walk(int64_t n, const int64_t *offp, const int32_t 
   for (int o = 16; o >= 1; o >>= 1) local += __shfl_down_sync(TR_FULL, local, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(acc, local);
 }
+// Sum over the oriented edges (u, v) of d+(u) + d+(v): the out-list entries
+// a forward merge of out(u) and out(v) reads for every edge.
+__global__ void k_count_merge(int64_t m, const int64_t *offp, const int32_t *esrc,
+                              const int32_t *adjp, unsigned long long *acc) {
+  unsigned long long local = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int u = esrc[e], v = adjp[e];
+    local += (unsigned long long)(offp[u + 1] - offp[u] + offp[v + 1] - offp[v]);
+  }
+  for (int o = 16; o >= 1; o >>= 1) local += __shfl_down_sync(TR_FULL, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(acc, local);
+}
 }  // namespace
 
-// Algorithmic bytes of the support pass: walk bytes + per triangle the
-// read-modify-write of e_uw's count (8 B) and, when recording, its 8-B
-// record.  Of the list pass: see below.
+// Algorithmic bytes of the support pass.  b_sup: 4 B per out-list entry of
+// the forward merge of every oriented edge, 32 B of offsets, 8 B of
+// endpoints and a 4-B support write per edge, and three 8-B read-modify-
+// writes per triangle.  b_sup_design: the walk this library runs (above)
+// plus, per triangle, the read-modify-write of e_uw's count (8 B) and, when
+// recording, its 8-B record.  Of the list pass: see below.
 int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records, bool in_place,
-                        double *b_sup, double *b_lists, cudaStream_t s) {
-  unsigned long long *acc = A.get<unsigned long long>(1);
+                        double *b_sup, double *b_sup_design, double *b_lists, cudaStream_t s) {
+  unsigned long long *acc = A.get<unsigned long long>(2);
   if (!acc) return TRUSS_ENOMEM;
-  TR_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
+  TR_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), s));
+  unsigned long long hm = 0;
+  if (g.m > 0) {
+    k_count_merge<<<grid_for(g.m, 256, 152 * 8), 256, 0, s>>>(g.m, g.offp, g.esrc, g.adjp,
+                                                               acc + 1);
+    TR_LAUNCHED();
+    TR_CUDA(cudaMemcpyAsync(&hm, acc + 1, sizeof(hm), cudaMemcpyDeviceToHost, s));
+  }
   if (g.n > 0 && g.m > 0) {
     k_count_walk<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, g.offp, acc);
     TR_LAUNCHED();
@@ -1037,7 +1060,8 @@ int count_support_bytes(Arena &A, const Csr &g, int64_t triangles, bool records,
   // per edge the rest lengths and their scan (32 B), the cursor set-up
   // (16 B) and both passes' reads (28 B).  Lists by a second walk: the walk
   // again plus 60 B per triangle.
-  *b_sup = (double)h + (records ? 16.0 : 8.0) * (double)triangles;
+  *b_sup = 4.0 * (double)hm + 44.0 * (double)g.m + 24.0 * (double)triangles;
+  *b_sup_design = (double)h + (records ? 16.0 : 8.0) * (double)triangles;
   *b_lists = !records  ? (double)hl + 60.0 * (double)triangles
              : in_place ? 48.0 * (double)triangles + 76.0 * (double)g.m
                         : 56.0 * (double)triangles + 56.0 * (double)g.m;

@@ -57,7 +57,11 @@ class truss_run_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("candidates", ctypes.c_int64),
                 ("rounds", ctypes.c_int32), ("lists_layout", ctypes.c_int32),
                 ("peel_entries", ctypes.c_int64), ("peel_decrements", ctypes.c_int64),
-                ("peel_scanned", ctypes.c_int64)]
+                ("peel_scanned", ctypes.c_int64), ("design_bytes_support", ctypes.c_double),
+                ("design_bytes_peel", ctypes.c_double), ("peel_sum_min_alive", ctypes.c_int64),
+                ("peel_sum_min_alive_start", ctypes.c_int64),
+                ("peel_alive_levels", ctypes.c_int64), ("peel_dead_entries", ctypes.c_int64),
+                ("peel_dead_earlier", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -86,7 +90,7 @@ class truss_serve_stats(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("wall_s", ctypes.c_double), ("edges_per_s", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("retried", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -206,6 +210,22 @@ def _len(x):
     return int(x.shape[0])
 
 
+def _rows(where, src, dst, *outs):
+    """Row count of src, after checking that dst and every per-row output
+    given (None = not given) have as many entries: a shorter buffer would be
+    read or written past its end by the library."""
+    rows = _len(src)
+    for name, x in (("dst", dst),) + tuple((f"output {i}", o) for i, o in enumerate(outs)):
+        if x is not None and _len(x) != rows:
+            raise TypeError(f"{where}: {name} has {_len(x)} entries, src has {rows}")
+    return rows
+
+
+def _at_least(where, name, x, count):
+    if x is not None and _len(x) < count:
+        raise TypeError(f"{where}: {name} has {_len(x)} entries, {count} needed")
+
+
 # ----------------------------------------------------------- entry points ---
 def truss_strerror(code: int) -> str:
     return _lib().truss_strerror(code).decode()
@@ -228,7 +248,7 @@ def truss_ctx_destroy(ctx) -> None:
 
 
 def truss_support(ctx, n: int, src, dst, support_out, stream=None) -> None:
-    rows = _len(src)
+    rows = _rows("truss_support", src, dst, support_out)
     _check(_lib().truss_support(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(support_out),
                                 _stream(stream, src, support_out)), "truss_support")
 
@@ -236,7 +256,8 @@ def truss_support(ctx, n: int, src, dst, support_out, stream=None) -> None:
 def truss_decompose(ctx, n: int, src, dst, support_out, truss_out, kmax_out=None,
                     stream=None) -> int:
     """Returns k_max (also written to kmax_out when given)."""
-    rows = _len(src)
+    rows = _rows("truss_decompose", src, dst, support_out, truss_out)
+    _at_least("truss_decompose", "kmax_out", kmax_out, 1)
     k = np.zeros(1, np.int32)
     kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
     _check(_lib().truss_decompose(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(support_out),
@@ -246,7 +267,7 @@ def truss_decompose(ctx, n: int, src, dst, support_out, truss_out, kmax_out=None
 
 
 def truss_upper_bound(ctx, n: int, src, dst, support_out, psi_out, stream=None) -> None:
-    rows = _len(src)
+    rows = _rows("truss_upper_bound", src, dst, support_out, psi_out)
     _check(_lib().truss_upper_bound(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(support_out),
                                     _ptr(psi_out), _stream(stream, src, psi_out)),
            "truss_upper_bound")
@@ -254,7 +275,8 @@ def truss_upper_bound(ctx, n: int, src, dst, support_out, psi_out, stream=None) 
 
 def truss_top(ctx, n: int, src, dst, t: int, truss_out, kmax_out=None, stream=None) -> int:
     """Returns k_max (also written to kmax_out when given)."""
-    rows = _len(src)
+    rows = _rows("truss_top", src, dst, truss_out)
+    _at_least("truss_top", "kmax_out", kmax_out, 1)
     k = np.zeros(1, np.int32)
     kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
     _check(_lib().truss_top(ctx, n, rows, _ptr(src), _ptr(dst), int(t), _ptr(truss_out), kp,
@@ -265,7 +287,8 @@ def truss_top(ctx, n: int, src, dst, t: int, truss_out, kmax_out=None, stream=No
 def truss_decompose_budget(ctx, n: int, src, dst, budget_edges: int, support_out, truss_out,
                            kmax_out=None, stream=None) -> int:
     """Returns k_max (also written to kmax_out when given)."""
-    rows = _len(src)
+    rows = _rows("truss_decompose_budget", src, dst, support_out, truss_out)
+    _at_least("truss_decompose_budget", "kmax_out", kmax_out, 1)
     k = np.zeros(1, np.int32)
     kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
     _check(_lib().truss_decompose_budget(ctx, n, rows, _ptr(src), _ptr(dst), int(budget_edges),
@@ -277,7 +300,9 @@ def truss_decompose_budget(ctx, n: int, src, dst, budget_edges: int, support_out
 
 def truss_core(ctx, n: int, src, dst, core_out, kmax_out=None, stream=None) -> int:
     """Core number per vertex into core_out (n entries); returns the largest."""
-    rows = _len(src)
+    rows = _rows("truss_core", src, dst)
+    _at_least("truss_core", "core_out", core_out, n)
+    _at_least("truss_core", "kmax_out", kmax_out, 1)
     k = np.zeros(1, np.int32)
     kp = _ptr(kmax_out) if kmax_out is not None else k.ctypes.data
     _check(_lib().truss_core(ctx, n, rows, _ptr(src), _ptr(dst), _ptr(core_out), kp,
@@ -291,6 +316,12 @@ def truss_decompose_batch(ctx, n, row_off, src, dst, support_out, truss_out, kma
     n = np.ascontiguousarray(n, np.int64)
     row_off = np.ascontiguousarray(row_off, np.int64)
     G = len(n)
+    if len(row_off) != G + 1:
+        raise TypeError(f"truss_decompose_batch: row_off has {len(row_off)} entries, {G + 1} needed")
+    rows = _rows("truss_decompose_batch", src, dst, support_out, truss_out)
+    if G > 0 and int(row_off[G]) != rows:
+        raise TypeError(f"truss_decompose_batch: row_off[G] = {int(row_off[G])}, src has {rows} rows")
+    _at_least("truss_decompose_batch", "kmax_out", kmax_out, G)
     _check(_lib().truss_decompose_batch(ctx, G, n.ctypes.data, row_off.ctypes.data, _ptr(src),
                                         _ptr(dst), _ptr(support_out), _ptr(truss_out),
                                         _ptr(kmax_out), _stream(stream, src, truss_out)),
@@ -306,9 +337,16 @@ def truss_last_stats(ctx) -> dict:
 def truss_support_noalloc(n: int, src, dst, support_out, stream=None) -> None:
     """Allocation-free support for small graphs (device-accessible buffers;
     see include/truss.h for the size limits and the shared-scratch rules)."""
-    _check(_lib().truss_support_noalloc(n, _len(src), _ptr(src), _ptr(dst), _ptr(support_out),
-                                        _stream(stream, src, support_out)),
-           "truss_support_noalloc")
+    rows = _rows("truss_support_noalloc", src, dst, support_out)
+    args = (n, rows, _ptr(src), _ptr(dst), _ptr(support_out), _stream(stream, src, support_out))
+    if not isinstance(src, np.ndarray) and src.is_cuda:
+        import torch
+        # the library launches on the current device: make it the tensors' one
+        with torch.cuda.device(src.device):
+            rc = _lib().truss_support_noalloc(*args)
+    else:
+        rc = _lib().truss_support_noalloc(*args)
+    _check(rc, "truss_support_noalloc")
 
 
 # ---------------------------------------------------------------- serving ---
@@ -326,7 +364,8 @@ def truss_serve_start(ctx, opts: truss_serve_opts | None = None):
 def truss_serve_submit(srv, n: int, src, dst) -> int:
     """Queue a request; src/dst must stay alive until it completes."""
     t = ctypes.c_uint64(0)
-    _check(_lib().truss_serve_submit(srv, n, _len(src), _ptr(src), _ptr(dst), ctypes.byref(t)),
+    rows = _rows("truss_serve_submit", src, dst)
+    _check(_lib().truss_serve_submit(srv, n, rows, _ptr(src), _ptr(dst), ctypes.byref(t)),
            "truss_serve_submit")
     return int(t.value)
 

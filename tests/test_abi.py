@@ -165,3 +165,28 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(c, "size")] == ctypes.sizeof(S), c
         for f, _ in S._fields_:
             assert got[(c, f)] == getattr(S, f).offset, (c, f)
+
+
+def test_binding_checks_buffer_lengths_before_any_call():
+    """A per-row buffer shorter than src would be read or written past its
+    end by the library: the binding refuses it before calling in."""
+    import numpy as np
+    from paper_1205_6693_gb300 import truss as T
+    src = np.array([0, 1, 2], np.int32)
+    dst = np.array([1, 2, 0], np.int32)
+    short = np.zeros(2, np.int32)
+    ok = np.zeros(3, np.int32)
+    with pytest.raises(TypeError):
+        T.truss_support_noalloc(3, src, dst, short)
+    with pytest.raises(TypeError):
+        T.truss_support_noalloc(3, src, short, ok)
+    with pytest.raises(TypeError):
+        T.truss_decompose(None, 3, src, dst, ok, short)
+    with pytest.raises(TypeError):
+        T.truss_support(None, 3, src, dst, short)
+    with pytest.raises(TypeError):
+        T.truss_core(None, 3, src, dst, short)
+    with pytest.raises(TypeError):
+        T.truss_decompose_batch(None, [3], [0, 3], src, dst, ok, short)
+    with pytest.raises(TypeError):
+        T.truss_decompose_batch(None, [3], [0, 2], src, dst, ok, ok)

@@ -121,3 +121,62 @@ def test_poll_and_stop_drains_queue(T):
     # stop with the rest queued or running: they are finished before the join
     stats = T.truss_serve_stop(srv)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
+
+
+def _clique(k, n=None):
+    iu, ju = np.triu_indices(k, k=1)
+    return (n or k), iu.astype(np.int32), ju.astype(np.int32)
+
+
+def test_dense_request_completes_or_fails_alone(T):
+    """Requests far denser in triangles than the admission projection assumes
+    (cliques K_300 and K_400: 4.5x and 6x their projected footprint) mixed
+    into concurrent small requests under a small budget.  Each dense request
+    either completes bit-exact or fails alone with TRUSS_ENOMEM; every other
+    request completes and matches the oracle."""
+    ctx = T.truss_ctx_create(0)
+    budget = 256 << 20
+    srv = T.truss_serve_start(ctx, _serve_opts(T, streams=3, hbm_budget_bytes=budget,
+                                                batch_rows=20000, max_batch=32))
+    T.truss_ctx_destroy(ctx)
+    small = _requests(30, seed=7)
+    er_n = 3000
+    es, ed = graphgen.er(er_n, 12000, seed=8)
+    perm = graphgen.permutation(er_n, seed=8, stream=1)
+    es, ed = graphgen.add_cliques(es, ed, perm[:60], [60])
+    reqs = small[:10] + [_clique(300)] + small[10:20] + [(er_n, es, ed)] + [_clique(400)] \
+        + small[20:]
+    dense = {10, 22}
+    for j in dense:
+        n, s, _ = reqs[j]
+        assert T.truss_serve_footprint(n, len(s)) < budget  # admitted on its projection
+    tickets = [None] * len(reqs)
+
+    def client():
+        for j, (n, s, d) in enumerate(reqs):
+            tickets[j] = T.truss_serve_submit(srv, n, s, d)
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    outcomes = {}
+    for j, (n, s, d) in enumerate(reqs):
+        sup = np.empty(len(s), np.int32)
+        tr = np.empty(len(s), np.int32)
+        try:
+            T.truss_serve_wait(srv, tickets[j], -1, sup, tr)
+        except T.TrussError as e:
+            assert j in dense and e.code == T.TRUSS_ENOMEM, (j, e)
+            outcomes[j] = "ENOMEM"
+            continue
+        ref = oracle.truss(n, s, d)
+        assert np.array_equal(sup, ref.support), j
+        assert np.array_equal(tr, ref.truss), j
+        outcomes[j] = "ok"
+    stats = T.truss_serve_stop(srv)
+    failed = sum(v == "ENOMEM" for v in outcomes.values())
+    assert stats["completed"] == len(reqs) - failed and stats["failed"] == failed
+    assert all(outcomes[j] == "ok" for j in range(len(reqs)) if j not in dense)
+    # K_300 exceeds twice its projection: its first run fails and it is run
+    # again alone with the whole budget, which it fits
+    assert outcomes[10] == "ok" and stats["retried"] >= 1
