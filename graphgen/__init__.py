@@ -5,7 +5,7 @@ vertex ids ``[0, n)``).  It contains none of the truss-decomposition
 arithmetic and imports neither the oracle nor the CUDA library.  The C source
 ``gen.c`` is compiled on first use with gcc into ``libgraphgen.so`` beside it.
 
-Workloads (their definitions are stated in the design doc's input recipe):
+Workloads (each fully defined by its seed, sizes and sampling rule below):
 
 * ``tiny()``  - Erdos-Renyi n=4,096, m=32,768 distinct pairs (seed 0) plus six
   planted cliques of sizes 8, 12, 16, 20, 24, 32 on disjoint vertex sets.
@@ -262,9 +262,13 @@ def chung_lu_weights(n: int, mean: float, cap: float, gamma: float):
     return c, w
 
 
-def large(n: int = 2 ** 24, mean_deg: int = 20, cap: float = 2.0 ** 16):
-    """Chung-Lu, exponent 2.1, first n*mean/2 distinct pairs (seed 2)."""
+def large(n: int = 2 ** 24, mean_deg: int = 20, cap: float = 2.0 ** 16, rows: int | None = None):
+    """Chung-Lu, exponent 2.1, first n*mean/2 distinct pairs (seed 2).  With
+    ``rows``, only the first ``rows`` of those rows (the rows are the distinct
+    pairs in sample order, so a prefix needs only a shorter sampling run)."""
     m = n * mean_deg // 2
+    if rows is not None:
+        m = min(m, int(rows))
     src, dst = chung_lu(n, m, float(mean_deg), cap, 2.1, seed=2, sorted_dedup=True)
     return n, src, dst
 

@@ -50,6 +50,11 @@ OBJECTIVE: dict[str, tuple[str, ...]] = {
 _lock = threading.Lock()
 
 
+# Schedules tuned on GB300 and shipped with the package: consulted when the
+# user's cache has no entry for the call's bucket.
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "schedules_gb300.json")
+
+
 def cache_path() -> str:
     p = os.environ.get("TRUSS_TUNE_CACHE")
     if p:
@@ -128,6 +133,19 @@ def lookup(key: str, rows: int, graphs: int = 1, cache: dict | None = None,
         if bd is None or dist < bd:
             best, bd = ent, dist
     return dict(best["opts"]) if best else None
+
+
+def lookup_any(key: str, rows: int, graphs: int = 1):
+    """(opts, source) for an exact bucket match: the user's cache first
+    ("cache"), then the schedules shipped with the package ("shipped"); else
+    (None, None)."""
+    got = lookup(key, rows, graphs, nearest=False)
+    if got is not None:
+        return got, "cache"
+    got = lookup(key, rows, graphs, cache=load(SHIPPED), nearest=False)
+    if got is not None:
+        return got, "shipped"
+    return None, None
 
 
 def search(run: Callable[[dict], tuple[dict, object]], reps: int = 2, min_gain: float = 0.03,

@@ -15,7 +15,7 @@ import bench  # noqa: E402
 
 
 def _profile():
-    path = os.path.join(ROOT, "profiles", "traffic_mid_rmat20.txt")
+    path = os.path.join(ROOT, "profiles", "traffic_mid.txt")
     sha, rows = None, []
     for ln in open(path):
         p = ln.split()
