@@ -732,9 +732,19 @@ def run_single(args, ws, rank, local):
     dst_h = torch.from_numpy(dst_np).pin_memory()
     sup_h = torch.empty(rows, dtype=torch.int32).pin_memory()
     tr_h = torch.empty(rows, dtype=torch.int32).pin_memory()
-    e2e_ms = _timed_steps(lambda: ctx.decompose(n, src_h, dst_h, sup_h, tr_h, stream=stream),
-                          args.steps, 1, stream, flush, dev, dist)
+    e2e_stage = {"build": [], "support": [], "lists": [], "peel": [], "scatter": []}
+    e2e_layout = []
+
+    def e2e_step():
+        ctx.decompose(n, src_h, dst_h, sup_h, tr_h, stream=stream)
+        st2 = ctx.stats()
+        for k in e2e_stage:
+            e2e_stage[k].append(st2["ms_" + k])
+        e2e_layout.append(st2["lists_layout"])
+
+    e2e_ms = _timed_steps(e2e_step, args.steps, 1, stream, flush, dev, dist)
     e2e_value = ws * m * args.steps / (_max_over_ranks(dist, dev, sum(e2e_ms)) / 1e3)
+    e2e_med = {k: round(statistics.median(v[1:]), 3) for k, v in e2e_stage.items()}
     ctx.close()
     del src, dst, sup, tr, src_h, dst_h, sup_h, tr_h
     torch.cuda.empty_cache()
@@ -806,7 +816,8 @@ def run_single(args, ws, rank, local):
                          "peel_scanned")}},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * rows,
-                "d2h_bytes_per_step": 8 * rows},
+                "d2h_bytes_per_step": 8 * rows,
+                "stage_ms_median": e2e_med, "lists_layout": e2e_layout[-1]},
         "gpu_launches": int(sum(launches[max(args.warmup, 0):])),
         "clocks": clocks,
         "batch": batch,

@@ -257,6 +257,9 @@ typedef struct truss_run_stats {
    * edge, and those whose triangle lost it in an earlier level */
   int64_t peel_sum_min_alive, peel_sum_min_alive_start, peel_alive_levels;
   int64_t peel_dead_entries, peel_dead_earlier;
+  /* device workspace the context holds after the call, and the most of it
+   * the call used at once (bytes) */
+  int64_t workspace_bytes, workspace_peak;
 } truss_run_stats;
 
 /* Statistics of the last successful call on this context. */

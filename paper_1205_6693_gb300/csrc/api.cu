@@ -56,11 +56,25 @@ void Arena::release_all() {
   for (auto &c : chunks_) cudaFree(c.p);
   chunks_.clear();
   handed_ = 0;
+  peak_ = 0;
 }
 
 void Arena::reset() {
+  size_t live = 0;
+  for (auto &c : chunks_) live += c.cap > 0;
+  if (live > 1 && peak_ > 0) {
+    const size_t want = peak_;
+    release_all();
+    char *p = nullptr;
+    if (cudaMalloc(&p, want) == cudaSuccess) {
+      chunks_.push_back(Chunk{p, want, 0});
+    } else {
+      cudaGetLastError();  // leave it to alloc() to grow again
+    }
+  }
   for (auto &c : chunks_) c.used = 0;
   handed_ = 0;
+  peak_ = 0;
 }
 
 size_t Arena::headroom(size_t free_dev) const {
@@ -105,6 +119,7 @@ void *Arena::alloc(size_t bytes) {
       void *p = c.p + c.used;
       c.used += bytes;
       handed_ += bytes;
+      if (handed_ > peak_) peak_ = handed_;
       return p;
     }
   }
@@ -112,10 +127,28 @@ void *Arena::alloc(size_t bytes) {
   char *p = nullptr;
   if (cudaMalloc(&p, cap) != cudaSuccess) {
     cudaGetLastError();  // clear the sticky-free allocation error
-    return nullptr;
+    // Chunks are cut to the sizes an earlier call asked for; a call that
+    // allocates in another order may find none that fits while most of them
+    // are still untouched since reset().  Give those back and retry once.
+    // They stay in the list as empty entries, so the chunk indices that
+    // mark() records keep their meaning.
+    bool freed = false;
+    for (auto &c : chunks_) {
+      if (c.used == 0 && c.cap > 0) {
+        cudaFree(c.p);
+        c.p = nullptr;
+        c.cap = 0;
+        freed = true;
+      }
+    }
+    if (!freed || cudaMalloc(&p, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
   }
   chunks_.push_back(Chunk{p, cap, bytes});
   handed_ += bytes;
+  if (handed_ > peak_) peak_ = handed_;
   return p;
 }
 
@@ -401,6 +434,8 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
     }
   }
   st.launches = tr::take_launches();
+  st.workspace_bytes = (int64_t)A.reserved();
+  st.workspace_peak = (int64_t)A.peak();
   if (ctx->opts.count_bytes) {
     double bs = 0, bsd = 0, bl = 0;
     TR_TRY(tr::count_support_bytes(A, g, st.triangles, so.tb != nullptr, so.in_place, &bs, &bsd,

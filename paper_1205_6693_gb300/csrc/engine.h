@@ -18,6 +18,11 @@ int64_t take_launches();
 // Device workspace: a list of cudaMalloc'd chunks handed out by bump
 // allocation.  reset() makes every chunk reusable without freeing it, so a
 // steady stream of calls of similar size allocates nothing after the first.
+// A call that needed more than one chunk leaves them folded into a single
+// chunk of that call's peak size at the next reset(): chunks cut to one
+// call's sizes fragment under a call that allocates in another order (a
+// host-buffer call stages its inputs first), and near full device memory
+// that fragmentation fails allocations that fit.
 class Arena {
  public:
   ~Arena();
@@ -30,6 +35,7 @@ class Arena {
   }
   size_t reserved() const;
   size_t unused() const;  // bytes of reserved chunks not handed out since reset()
+  size_t peak() const { return peak_; }  // most bytes handed out at once since reset()
   // Cap on the bytes handed out since reset() (0 = none): alloc() returns
   // nullptr rather than exceed it.
   void set_limit(size_t bytes) { limit_ = bytes; }
@@ -51,6 +57,7 @@ class Arena {
   std::vector<Chunk> chunks_;
   size_t limit_ = 0;
   size_t handed_ = 0;  // bytes handed out since reset()
+  size_t peak_ = 0;    // most bytes handed out at once since reset()
 };
 
 // ------------------------------------------------------------ CUB glue ---

@@ -204,7 +204,8 @@ struct SupVArgs {
   const int64_t *inoff;   // [n+1] start of each head's group
   const int64_t *wpre;    // [m+1] exclusive prefix of the walk cost, in inedge order
   int64_t W, P;
-  int stage_max;
+  int stage_max;  // out-lists staged with their counts up to this many entries
+  int hash_max;   // longer ones get a shared table of positions up to this many
   int32_t *supA, *supB;
   // optional: per edge e = (u, v), the triangles (u, v, w) it closes, as
   // (e_uw, e_vw) records in tb[tbpre[e] .. tbpre[e] + cuv[e])
@@ -213,17 +214,25 @@ struct SupVArgs {
   int32_t *cuv;
 };
 
-// Position of w in out(v) (staged: hash table Hs of size 2^(32-sh) over Ls;
-// else a branch-free search of the global list), or -1.
-template <bool STAGED>
+// How a head's out(v) is searched: kSearch = branch-free search of the
+// global list; kStaged = out(v) and its counts in shared memory with a hash
+// table of positions; kHashOnly = a shared hash table of positions only
+// (the warp's whole buffer), hits checked against the global list (L1) and
+// counted with global atomics, for heads too long to stage.
+constexpr int kSearch = 0, kStaged = 1, kHashOnly = 2;
+constexpr int kHashOnlyCap = (int)(kHeadSmem / 2 / 2);  // heads up to this many entries
+
+// Position of w in out(v) (kStaged: hash table Hs of size 2^(32-sh) over Ls;
+// kHashOnly: the same over the global list gl), or -1.
+template <int MODE>
 __device__ __forceinline__ int find_in_out(int w, const int32_t *Ls, const unsigned short *Hs,
                                            int S, int sh, const int32_t *gl, int d) {
-  if (STAGED) {
+  if (MODE != kSearch) {
     unsigned sl = hslot(w, sh);
     for (;;) {
       const int p = Hs[sl];
       if (p == 0) return -1;
-      if (Ls[p - 1] == w) return p - 1;
+      if ((MODE == kStaged ? Ls[p - 1] : __ldg(&gl[p - 1])) == w) return p - 1;
       sl = (sl + 1) & (unsigned)(S - 1);
     }
   } else {
@@ -243,17 +252,17 @@ constexpr int kFlatU = 4;  // flattened steps whose loads are issued together
 
 // One hit of the walk: triangle (u, v, w) with e_uw = euw and e_vw at
 // position q of out(v), recorded at slot `slot` of e_uv's region.
-template <bool STAGED>
+template <int MODE>
 __device__ __forceinline__ void count_hit(const SupVArgs &a, int32_t *Cs, int64_t bv, int q,
                                           int64_t euw, int64_t slot) {
-  if (STAGED) atomicAdd(&Cs[q], 1);
+  if (MODE == kStaged) atomicAdd(&Cs[q], 1);
   else atomicAdd(&a.supB[bv + q], 1);
   atomicAdd(&a.supA[euw], 1);
   if (a.tb) a.tb[slot] = make_int2((int)euw, (int)(bv + q));
 }
 
 // The in-edges inedge[i0 .. i1) of head v (bv = offp[v], dv = |out(v)|).
-template <bool STAGED>
+template <int MODE>
 __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t i1, int64_t bv,
                                           int dv, int vmax, const int32_t *Ls, int32_t *Cs,
                                           const unsigned short *Hs, int S, int sh) {
@@ -291,7 +300,7 @@ __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t
       for (int k = 0; k < kFlatU; k++) {
         const int tr = t0 + k * 32;  // step of lane 0 in this round
         const int q =
-            w[k] <= vmax ? find_in_out<STAGED>(w[k], Ls, Hs, S, sh, a.adjp + bv, dv) : -1;
+            w[k] <= vmax ? find_in_out<MODE>(w[k], Ls, Hs, S, sh, a.adjp + bv, dv) : -1;
         const unsigned hm = __ballot_sync(TR_FULL, q >= 0);
         if (hm == 0) continue;
         const int prior = __shfl_sync(TR_FULL, mycnt, own[k]);
@@ -302,7 +311,7 @@ __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t
           const int lo = max(bo[k] - tr, 0);
           const unsigned below = hm & lt & ~((1u << lo) - 1u);
           const int64_t euw = (int64_t)eo + 1 + (tr + lane - bo[k]);
-          count_hit<STAGED>(a, Cs, bv, q, euw, tbase + prior + __popc(below));
+          count_hit<MODE>(a, Cs, bv, q, euw, tbase + prior + __popc(below));
         }
         // owners add this round's hits of their own walk
         if (sl > 0) {
@@ -341,10 +350,10 @@ __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t
 #pragma unroll
         for (int k = 0; k < 4; k++) {
           const int q =
-              w[k] <= vmax ? find_in_out<STAGED>(w[k], Ls, Hs, S, sh, a.adjp + bv, dv) : -1;
+              w[k] <= vmax ? find_in_out<MODE>(w[k], Ls, Hs, S, sh, a.adjp + bv, dv) : -1;
           const unsigned hm = __ballot_sync(TR_FULL, q >= 0);
           if (q >= 0)
-            count_hit<STAGED>(a, Cs, bv, q, start + t0 + k * 32 + lane,
+            count_hit<MODE>(a, Cs, bv, q, start + t0 + k * 32 + lane,
                               tbase + cnt + __popc(hm & lt));
           cnt += __popc(hm);
         }
@@ -400,16 +409,33 @@ __global__ void __launch_bounds__(kBlock, 3) k_support_v(SupVArgs a) {
             sl = (sl + 1) & (unsigned)(S - 1);
         }
         __syncwarp();
-        head_walk<true>(a, i0, iend, bv, dv, Ls[dv - 1], Ls, Cs, Hs, S, sh);
+        head_walk<kStaged>(a, i0, iend, bv, dv, Ls[dv - 1], Ls, Cs, Hs, S, sh);
         __syncwarp();
         for (int q = lane; q < dv; q += 32) {
           if (whole) a.supB[bv + q] = Cs[q];
           else if (Cs[q] != 0) atomicAdd(&a.supB[bv + q], Cs[q]);
         }
         __syncwarp();
+      } else if (dv <= a.hash_max) {
+        // the warp's whole buffer as a table of 2^lg >= 2 dv position slots
+        unsigned short *H2 = (unsigned short *)base;
+        int lg = 32 - __clz(2 * dv - 1);
+        lg = min(lg, 31 - __clz(kHashOnlyCap * 2));
+        const int S = 1 << lg, sh = 32 - lg;
+        for (int t = lane; t < S / 2; t += 32) ((uint32_t *)H2)[t] = 0u;
+        __syncwarp();
+        for (int q = lane; q < dv; q += 32) {
+          unsigned sl = hslot(__ldg(&a.adjp[bv + q]), sh);
+          while (atomicCAS(&H2[sl], (unsigned short)0, (unsigned short)(q + 1)) != 0)
+            sl = (sl + 1) & (unsigned)(S - 1);
+        }
+        __syncwarp();
+        head_walk<kHashOnly>(a, i0, iend, bv, dv, __ldg(&a.adjp[bv + dv - 1]), nullptr,
+                             nullptr, H2, S, sh);
+        __syncwarp();
       } else {
-        head_walk<false>(a, i0, iend, bv, dv, __ldg(&a.adjp[bv + dv - 1]), nullptr, nullptr,
-                         nullptr, 0, 0);
+        head_walk<kSearch>(a, i0, iend, bv, dv, __ldg(&a.adjp[bv + dv - 1]), nullptr, nullptr,
+                           nullptr, 0, 0);
       }
     }
   }
@@ -531,39 +557,94 @@ __global__ void k_walk_cost(int64_t m, const int64_t *offp, const int32_t *adjp,
   }
 }
 
-// Dense triangle lists from the records, in two passes so that the scattered
-// 8-byte list writes of each pass land in a small window of `pairs` that L2
-// can merge into whole sectors before they reach DRAM.  The first cuv[x]
+// Dense triangle lists from the records, in two passes.  The first cuv[x]
 // entries of edge x's list are the triangles x closes as the walked edge, in
 // record order: its records themselves, which stay where the walk wrote
 // them, unless the full lists are asked for (then they are copied to
-// pairs[toff[x] ..)).  cur[x] hands out the slots of the rest, the triangles
-// in which x is e_uw or e_vw.
+// pairs[toff[x] ..)).  The rest are handed out from x's cursor cur[x] (set
+// to the first slot after the own part).
 //
-// Pass 1 (k_lists_from_records, edges in id order = grouped by owner u): for
-// each record (e_uw, e_vw) of walked edge e_uv it writes e_uw's entry (and,
-// for the full lists, e_uv's own entry); e_uw lies in out(u), whose lists
-// are one contiguous stretch of `pairs`.
-// Pass 2 (k_lists_vw, walked edges grouped by their head v): e_vw's entry;
-// e_vw lies in out(v), so a warp working on v's in-edges writes into v's
-// stretch.
-// A warp takes 32 consecutive entries of an edge order at a time and walks
-// their records 4 per lane per step, so that 4 record loads and then 4
-// cursor atomics are in flight per lane before any store needs their results.
+// Pass 1 (k_lists_owner) writes, for each record (e_uw, e_vw) of walked edge
+// e_uv, e_uw's entry (e_uv, e_vw) (and, for the full lists, e_uv's own
+// entry).  e_uw lies in out(u), so every cursor pass 1 touches for the
+// records of u's out-edges is one of u's out-edges.  Pass 2 (k_lists_head)
+// writes e_vw's entry (e_uv, e_uw); e_vw lies in out(v), so the records of
+// v's in-edges touch only cursors of v's out-edges.  Each pass therefore
+// splits the vertices (owners u, heads v) into ranges of about equal record
+// counts, and one block takes a whole range: the cursors of the range's
+// out-edges (at most a few thousand, since in degree order an out-degree d
+// needs d neighbours of degree >= d) are counted in shared memory, with no
+// global atomic, and each range's list writes land in the range's own
+// stretch of `pairs`, which L2 merges into whole sectors.  A range with more
+// out-edges than the shared counters hold (a vertex of huge out-degree)
+// falls back to global atomics on its cursors.  Pass 1 adds its counts to
+// the cursors at the end of each range, so pass 2 continues after them.
+//
+// Within a range the warps claim chunks of consecutive edges (pass 1) or
+// in-edges (pass 2) from a shared counter, and walk a chunk's records 4 per
+// lane per step, so that 4 record loads are in flight per lane before any
+// store needs them.  A chunk holds up to 32 edges, fewer in a range whose
+// edges carry many records (about 256 records per chunk), so that a range
+// of a few heavy edges still keeps every warp of the block busy.
 constexpr int kListU = 4;
+constexpr int kLBlock = 512;
+constexpr int kLCap = 16384;       // shared cursor counters per range (64 KB)
+constexpr int kLEdgeCost = 4;      // range cost per edge (next to its records)
+constexpr int64_t kLRangeCost = (int64_t)kLCap * kLEdgeCost / 2;
 
-// toff = null: the own parts stay in place and only partner entries are written.
-__global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2 *tb,
-                                     const int32_t *cuv, const int64_t *toff,
-                                     unsigned long long *cur, int2 *pairs, uint32_t *tids,
-                                     int64_t entries, int *err) {
+struct ListPass {
+  int64_t m, n;
+  const int64_t *offp;
+  const int64_t *tbpre;
+  const int2 *tb;
+  const int32_t *cuv;
+  const int64_t *toff;        // pass 1, whole lists: own slots; null with own parts in place
+  unsigned long long *cur;    // per edge: next free slot of its rest part
+  const int32_t *inedge;      // pass 2: edges grouped by head
+  const int64_t *inoff;
+  const int64_t *vb;          // range r = vertices [vb[r], vb[r+1])
+  const int64_t *pre;         // exclusive prefix of (records + kLEdgeCost) over the walk order
+  int64_t nranges;
+  unsigned long long *next;   // range counter
+  int2 *pairs;
+  uint32_t *tids;
+  int64_t entries;
+  int *err;
+};
+
+__device__ __forceinline__ void pairs_store(const ListPass &a, int64_t x, int2 v, uint32_t tid) {
+  a.pairs[x] = v;
+  if (a.tids) a.tids[x] = tid;
+}
+
+// One range of a pass; HEAD = pass 2.  Every thread of the block calls it.
+template <bool HEAD>
+__device__ __forceinline__ void list_range(const ListPass &a, int64_t v0, int64_t v1,
+                                           int *s_ctr, int *s_next) {
   const int lane = lane_id();
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = gw * 32; base < m; base += nw * 32) {
-    const int64_t e = base + lane;
-    const int c = e < m ? cuv[e] : 0;
-    const int64_t r0 = e < m ? tbpre[e] : 0, l0 = (e < m && toff) ? toff[e] : 0;
+  const int64_t e0 = a.offp[v0], e1 = a.offp[v1], ne = e1 - e0;
+  const bool local = ne <= kLCap;
+  if (local)
+    for (int64_t i = threadIdx.x; i < ne; i += blockDim.x) s_ctr[i] = 0;
+  if (threadIdx.x == 0) *s_next = 0;
+  __syncthreads();
+  // pass 1 walks the edges [e0, e1); pass 2 the in-edges of the heads
+  const int64_t w0 = HEAD ? a.inoff[v0] : e0, w1 = HEAD ? a.inoff[v1] : e1;
+  const int64_t recs = a.pre[w1] - a.pre[w0] - kLEdgeCost * (w1 - w0);
+  const int64_t cw = (256 * (w1 - w0)) / (recs > 0 ? recs : 1);
+  const int chunk = cw < 1 ? 1 : cw > 32 ? 32 : (int)cw;
+  for (;;) {
+    int ci = 0;
+    if (lane == 0) ci = atomicAdd(s_next, 1);
+    ci = __shfl_sync(TR_FULL, ci, 0);
+    const int64_t base = w0 + (int64_t)ci * chunk;
+    if (base >= w1) break;
+    const int64_t i = base + lane;
+    const bool in = lane < chunk && i < w1;
+    const int e = in ? (HEAD ? __ldg(&a.inedge[i]) : (int)i) : 0;
+    const int c = in ? __ldg(&a.cuv[e]) : 0;
+    const int64_t r0 = in ? __ldg(&a.tbpre[e]) : 0;
+    const int64_t l0 = (!HEAD && in && a.toff) ? __ldg(&a.toff[e]) : 0;
     const int P = warp_incl_scan(c);
     const int total = __shfl_sync(TR_FULL, P, 31);
     for (int t0 = 0; t0 < total; t0 += 32 * kListU) {
@@ -575,86 +656,96 @@ __global__ void k_lists_from_records(int64_t m, const int64_t *tbpre, const int2
       for (int k = 0; k < kListU; k++) {
         const int t = t0 + k * 32 + lane;
         const int o = warp_owner(P, t < total ? t : total - 1);
-        const int64_t orr = __shfl_sync(TR_FULL, r0, o), ol = __shfl_sync(TR_FULL, l0, o);
-        const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
-        const int j = t - (oP - oc);
-        eo[k] = (int)(base + o);
-        x1[k] = ol + j;
-        ri[k] = (uint32_t)(orr + j);
-        rec[k] = t < total ? __ldg(&tb[orr + j]) : make_int2(-1, -1);  // (e_uw, e_vw) on e_uv
-      }
-#pragma unroll
-      for (int k = 0; k < kListU; k++)
-        x2[k] = rec[k].x >= 0 ? (int64_t)atomicAdd(&cur[rec[k].x], 1ull) : 0;
-#pragma unroll
-      for (int k = 0; k < kListU; k++) {
-        if (rec[k].x < 0) continue;
-        if ((!toff || x1[k] < entries) && x2[k] < entries) {
-          if (toff) pairs[x1[k]] = rec[k];
-          pairs[x2[k]] = make_int2(eo[k], rec[k].y);
-          if (tids) {
-            tids[x1[k]] = ri[k];
-            tids[x2[k]] = ri[k];
-          }
-        } else {
-          atomicExch(err, TRUSS_ECHECK);
-        }
-      }
-    }
-  }
-}
-
-// inedge[0 .. m) = the oriented edges sorted by head v (pass 2's order).
-__global__ void k_lists_vw(int64_t m, const int32_t *inedge, const int64_t *tbpre,
-                           const int2 *tb, const int32_t *cuv, unsigned long long *cur,
-                           int2 *pairs, uint32_t *tids, int64_t entries, int *err) {
-  const int lane = lane_id();
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = gw * 32; base < m; base += nw * 32) {
-    const int64_t i = base + lane;
-    const int e = i < m ? __ldg(&inedge[i]) : 0;
-    const int c = i < m ? __ldg(&cuv[e]) : 0;
-    const int64_t r0 = i < m ? __ldg(&tbpre[e]) : 0;
-    const int P = warp_incl_scan(c);
-    const int total = __shfl_sync(TR_FULL, P, 31);
-    for (int t0 = 0; t0 < total; t0 += 32 * kListU) {
-      int2 rec[kListU];
-      int64_t x3[kListU];
-      int eo[kListU];
-      uint32_t ri[kListU];
-#pragma unroll
-      for (int k = 0; k < kListU; k++) {
-        const int t = t0 + k * 32 + lane;
-        const int o = warp_owner(P, t < total ? t : total - 1);
         const int64_t orr = __shfl_sync(TR_FULL, r0, o);
+        const int64_t ol = __shfl_sync(TR_FULL, l0, o);
         const int oP = __shfl_sync(TR_FULL, P, o), oc = __shfl_sync(TR_FULL, c, o);
         eo[k] = __shfl_sync(TR_FULL, e, o);
         const int j = t - (oP - oc);
+        x1[k] = ol + j;
         ri[k] = (uint32_t)(orr + j);
-        rec[k] = t < total ? __ldg(&tb[orr + j]) : make_int2(-1, -1);
+        rec[k] = t < total ? __ldg(&a.tb[orr + j]) : make_int2(-1, -1);  // (e_uw, e_vw)
       }
 #pragma unroll
-      for (int k = 0; k < kListU; k++)
-        x3[k] = rec[k].y >= 0 ? (int64_t)atomicAdd(&cur[rec[k].y], 1ull) : 0;
+      for (int k = 0; k < kListU; k++) {
+        const int f = HEAD ? rec[k].y : rec[k].x;  // the edge whose cursor hands out the slot
+        x2[k] = 0;
+        if (f < 0) continue;
+        const int64_t fi = (int64_t)f - e0;
+        if (fi < 0 || fi >= ne) {
+          atomicExch(a.err, TRUSS_ECHECK);  // a record outside its range: skip it
+          rec[k] = make_int2(-1, -1);
+          continue;
+        }
+        x2[k] = local ? (int64_t)a.cur[f] + atomicAdd(&s_ctr[fi], 1)
+                      : (int64_t)atomicAdd(&a.cur[f], 1ull);
+      }
 #pragma unroll
       for (int k = 0; k < kListU; k++) {
-        if (rec[k].y < 0) continue;
-        if (x3[k] < entries) {
-          pairs[x3[k]] = make_int2(eo[k], rec[k].x);
-          if (tids) tids[x3[k]] = ri[k];
+        if (rec[k].x < 0) continue;
+        const bool own = !HEAD && a.toff;
+        if ((!own || x1[k] < a.entries) && x2[k] < a.entries) {
+          if (own) pairs_store(a, x1[k], rec[k], ri[k]);
+          pairs_store(a, x2[k], HEAD ? make_int2(eo[k], rec[k].x) : make_int2(eo[k], rec[k].y),
+                      ri[k]);
         } else {
-          atomicExch(err, TRUSS_ECHECK);
+          atomicExch(a.err, TRUSS_ECHECK);
         }
       }
     }
   }
+  __syncthreads();
+  // pass 1: later passes continue after this range's slots
+  if (!HEAD && local)
+    for (int64_t i = threadIdx.x; i < ne; i += blockDim.x) a.cur[e0 + i] += (unsigned)s_ctr[i];
 }
 
-__global__ void k_edge_ids(int64_t m, int32_t *ids) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x)
-    ids[e] = (int32_t)e;
+template <bool HEAD>
+__global__ void __launch_bounds__(kLBlock, 2) k_lists_pass(ListPass a) {
+  extern __shared__ int s_ctr[];
+  __shared__ long long s_r;
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_r = (long long)atomicAdd(a.next, 1ull);
+    __syncthreads();
+    const int64_t r = s_r;
+    if (r >= a.nranges) return;
+    const int64_t v0 = a.vb[r], v1 = a.vb[r + 1];
+    if (v0 < v1) list_range<HEAD>(a, v0, v1, s_ctr, &s_next);  // ends with a block barrier
+    else __syncthreads();
+  }
+}
+
+// Range costs of the two passes: pass 1 per edge e (grouped by owner),
+// cuv[e] + kLEdgeCost; pass 2 per in-edge position i, cuv[inedge[i]] +
+// kLEdgeCost (and kLEdgeCost per out-edge of each head, added below).
+__global__ void k_list_costs(int64_t m, const int32_t *cuv, const int32_t *inedge, int64_t *c1,
+                             int64_t *c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    c1[i] = i < m ? (int64_t)cuv[i] + kLEdgeCost : 0;
+    c2[i] = i < m ? (int64_t)cuv[inedge[i]] + kLEdgeCost : 0;
+  }
+}
+
+// vb[r] = first vertex v with cost(v) >= r * kLRangeCost, for r < nr, and
+// vb[nr] = n; cost(v) = pre[idx[v]] (+ kLEdgeCost * offp[v] for pass 2).
+__global__ void k_list_ranges(int64_t n, int64_t nr, const int64_t *pre, const int64_t *idx,
+                              const int64_t *offp, bool head, int64_t *vb) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= nr;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    if (r == nr) {
+      vb[r] = n;
+      continue;
+    }
+    const int64_t x = r * kLRangeCost;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      const int64_t c = pre[idx[mid]] + (head ? kLEdgeCost * offp[mid] : 0);
+      if (c < x) lo = mid + 1; else hi = mid;
+    }
+    vb[r] = lo;
+  }
 }
 
 // Cursors for the list passes: the first slot after each edge's own part
@@ -742,6 +833,7 @@ int launch_walk_v(SupVArgs a, const SupportCfg &cfg, cudaStream_t s) {
   if (P > a.m) P = a.m > 0 ? a.m : 1;
   a.P = P;
   a.stage_max = cfg.stage_max > 0 && cfg.stage_max < kHeadCap ? cfg.stage_max : kHeadCap;
+  a.hash_max = kHashOnlyCap;
   k_support_v<<<grid, kBlock, smem, s>>>(a);
   TR_LAUNCHED();
   return TRUSS_OK;
@@ -791,11 +883,13 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
       TR_CUDA(cudaMemcpyAsync(&R, tbpre + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TR_CUDA(cudaStreamSynchronize(s));
   }
-  // Records need 8 R bytes now, and the lists later at most 24 R more when
-  // they are whole, 16 R with the own parts left in the records, plus a few
-  // words per edge for the list passes.  Whole lists when they fit (their
-  // peel reads one stretch per edge), else own parts in place when those
-  // fit, else no records (the list pass walks the graph a second time).
+  // Records need 8 R bytes now, and the lists later 24 bytes per triangle
+  // when they are whole, 16 with the own parts left in the records, plus a
+  // few words per edge for the list passes and the peel.  The walk records
+  // only if the lists fit at their bound (a triangle per record slot, T <=
+  // R); otherwise the list pass walks the graph a second time.  Whole lists
+  // or own parts in place is decided after the walk, from the exact
+  // triangle count (the bound can be twice the count or more).
   int2 *recs = nullptr;
   int32_t *cuv = nullptr;
   bool in_place = false;
@@ -808,14 +902,7 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
     const double avail = (double)A.headroom(fr);
     const double need_whole = 1.05 * (32.0 * (double)R + 20.0 * (double)m);
     const double need_in_place = 1.05 * (24.0 * (double)R + 36.0 * (double)m);
-    bool use = false;
-    if (cfg.full_lists) {
-      use = need_whole < avail;
-    } else if (!cfg.in_place && need_whole < avail) {
-      use = true;
-    } else if (need_in_place < avail) {
-      use = in_place = true;
-    }
+    const bool use = cfg.full_lists ? need_whole < avail : need_in_place < avail;
     if (use) {
       recs = A.get<int2>(R);
       cuv = A.get<int32_t>(m);
@@ -863,6 +950,21 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
   out->entries = total;
   out->inedge = inedge;
   out->inoff = inoff;
+  if (recs && !cfg.full_lists) {
+    if (cfg.in_place) {
+      in_place = true;
+    } else {
+      // whole lists: 3T entries, the peel's work items (up to 3T/16 + m, two
+      // queues) and about 100 B per edge for the list passes and the peel
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        fr = 0;
+      }
+      const double tri = (double)(total / 3);
+      in_place = !(1.05 * (30.0 * tri + 100.0 * (double)m) < (double)A.headroom(fr));
+    }
+  }
   out->tbpre = recs ? tbpre : nullptr;
   out->records = recs ? R : 0;
   out->tb = recs;
@@ -906,17 +1008,69 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
       k_cursors_rec<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(m, so.toff, so.cuv, cur);
       TR_LAUNCHED();
     }
-    // pass 2 walks the edges grouped by head (the support walk's index)
-    const int32_t *inedge = so.inedge;
+    // vertex ranges of about kLRangeCost: pass 1 over owners (edge order),
+    // pass 2 over heads (the support walk's in-edge index)
+    const int64_t n = g.n, tri = so.entries / 3;
+    int64_t *c1 = A.get<int64_t>(m + 1), *c2 = A.get<int64_t>(m + 1);
+    int64_t *p1 = A.get<int64_t>(m + 1), *p2 = A.get<int64_t>(m + 1);
+    const int64_t nr1 = (tri + kLEdgeCost * m) / kLRangeCost + 1;
+    const int64_t nr2 = (tri + 2 * kLEdgeCost * m) / kLRangeCost + 1;
+    int64_t *vb1 = A.get<int64_t>(nr1 + 1), *vb2 = A.get<int64_t>(nr2 + 1);
+    unsigned long long *next = A.get<unsigned long long>(2);
+    if (!c1 || !c2 || !p1 || !p2 || !vb1 || !vb2 || !next) return TRUSS_ENOMEM;
+    k_list_costs<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, so.cuv, so.inedge, c1, c2);
+    TR_LAUNCHED();
+    size_t tb = 0;
+    TR_TRY(exclusive_sum_i64(nullptr, &tb, c1, p1, m + 1, s));
+    void *tmp = A.alloc(tb);
+    if (!tmp) return TRUSS_ENOMEM;
+    TR_TRY(exclusive_sum_i64(tmp, &tb, c1, p1, m + 1, s));
+    TR_TRY(exclusive_sum_i64(tmp, &tb, c2, p2, m + 1, s));
+    k_list_ranges<<<grid_for(nr1 + 1, 256, 152 * 8), 256, 0, s>>>(n, nr1, p1, g.offp, g.offp,
+                                                                    false, vb1);
+    TR_LAUNCHED();
+    k_list_ranges<<<grid_for(nr2 + 1, 256, 152 * 8), 256, 0, s>>>(n, nr2, p2, so.inoff, g.offp,
+                                                                    true, vb2);
+    TR_LAUNCHED();
+    TR_CUDA(cudaMemsetAsync(next, 0, 2 * sizeof(unsigned long long), s));
     int dev = 0, sms = cfg.sms;
     TR_CUDA(cudaGetDevice(&dev));
     if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    k_lists_from_records<<<sms * 8, 256, 0, s>>>(m, so.tbpre, so.tb, so.cuv,
-                                                 in_place ? nullptr : so.toff, cur, pairs, tids,
-                                                 rest, err);
+    const size_t smem = sizeof(int) * kLCap;
+    TR_CUDA(cudaFuncSetAttribute(k_lists_pass<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TR_CUDA(cudaFuncSetAttribute(k_lists_pass<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    TR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lists_pass<false>, kLBlock,
+                                                          smem));
+    if (occ < 1) occ = 1;
+    ListPass lp{};
+    lp.m = m;
+    lp.n = n;
+    lp.offp = g.offp;
+    lp.tbpre = so.tbpre;
+    lp.tb = so.tb;
+    lp.cuv = so.cuv;
+    lp.toff = in_place ? nullptr : so.toff;
+    lp.cur = cur;
+    lp.inedge = so.inedge;
+    lp.inoff = so.inoff;
+    lp.pairs = pairs;
+    lp.tids = tids;
+    lp.entries = rest;
+    lp.err = err;
+    lp.vb = vb1;
+    lp.pre = p1;
+    lp.nranges = nr1;
+    lp.next = next;
+    k_lists_pass<false><<<sms * occ, kLBlock, smem, s>>>(lp);
     TR_LAUNCHED();
-    k_lists_vw<<<sms * 8, 256, 0, s>>>(m, inedge, so.tbpre, so.tb, so.cuv, cur, pairs, tids,
-                                       rest, err);
+    lp.vb = vb2;
+    lp.pre = p2;
+    lp.nranges = nr2;
+    lp.next = next + 1;
+    k_lists_pass<true><<<sms * occ, kLBlock, smem, s>>>(lp);
     TR_LAUNCHED();
     int h_err = 0;
     TR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));

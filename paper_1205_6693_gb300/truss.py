@@ -61,7 +61,8 @@ class truss_run_stats(ctypes.Structure):
                 ("design_bytes_peel", ctypes.c_double), ("peel_sum_min_alive", ctypes.c_int64),
                 ("peel_sum_min_alive_start", ctypes.c_int64),
                 ("peel_alive_levels", ctypes.c_int64), ("peel_dead_entries", ctypes.c_int64),
-                ("peel_dead_earlier", ctypes.c_int64)]
+                ("peel_dead_earlier", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("workspace_peak", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -420,3 +420,32 @@ def test_barrier_free_peel_bounded_wait():
         assert_same(c2, n, src, dst)
     finally:
         c2.close()
+
+
+def test_workspace_settles_after_calls_of_another_order():
+    """The context's workspace is one chunk of the peak size once a call has
+    needed several, so calls of the same shape reuse it without allocating,
+    also after a host-buffer call (which stages its inputs first)."""
+    from paper_1205_6693_gb300 import truss as T
+    n, src, dst = 1 << 14, *graphgen.rmat_raw(14, 16 << 14, seed=9)
+    dev = torch.device("cuda:0")
+    s, d = torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev)
+    sup, tr = torch.empty_like(s), torch.empty_like(s)
+    c = T.Context(0)
+    try:
+        seen = []
+        for host in (False, False, False, True, True, True, False, False):
+            if host:
+                hs, ht = np.empty(len(src), np.int32), np.empty(len(src), np.int32)
+                c.decompose(n, src, dst, hs, ht)
+            else:
+                c.decompose(n, s, d, sup, tr)
+            st = c.stats()
+            assert 0 < st["workspace_peak"] <= st["workspace_bytes"]
+            seen.append(st["workspace_bytes"])
+        # steady within each run of same-shaped calls: no growth after the first two
+        assert seen[1] == seen[2] and seen[4] == seen[5] and seen[6] == seen[7], seen
+        ref = oracle.truss(n, src, dst)
+        assert np.array_equal(tr.cpu().numpy(), ref.truss)
+    finally:
+        c.close()
