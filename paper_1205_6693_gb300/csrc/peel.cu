@@ -255,7 +255,14 @@ __device__ __forceinline__ void decide(const PeelArgs &a, bool valid, int e, int
     atomicExch(&a.ctl->err, TRUSS_ECHECK);  // corrupt list entry: skip it
     return;
   }
-  const int s1 = __ldcg(&a.stamp[p1]), s2 = __ldcg(&a.stamp[p2]);
+  // more than half the entries read belong to triangles that already lost
+  // an edge: partner 2's state is read only if partner 1 is still there
+  const int s1 = __ldcg(&a.stamp[p1]);
+  if (s1 != 0 && s1 != ts && s1 != tn) {
+    dead = true;
+    return;
+  }
+  const int s2 = __ldcg(&a.stamp[p2]);
   const bool dead1 = s1 != 0 && s1 != ts && s1 != tn, dead2 = s2 != 0 && s2 != ts && s2 != tn;
   dead = dead1 || dead2;
   if (dead) return;
