@@ -319,6 +319,10 @@ def batch_section(args, ws, rank, local, dev, dist):
     g0, g1 = shard_range(args.graphs, rank, ws)
     ns, off, src_np, dst_np = graphgen.batch(g1 - g0, first=g0)
     G, rows = len(ns), int(off[-1])
+    src_h, dst_h = torch.from_numpy(src_np).pin_memory(), torch.from_numpy(dst_np).pin_memory()
+    sup_h = torch.empty(rows, dtype=torch.int32).pin_memory()
+    tr_h = torch.empty(rows, dtype=torch.int32).pin_memory()
+    km_h = torch.empty(G, dtype=torch.int32).pin_memory()
     src = torch.from_numpy(src_np).to(dev)
     dst = torch.from_numpy(dst_np).to(dev)
     sup, tr = torch.empty_like(src), torch.empty_like(src)
@@ -348,10 +352,6 @@ def batch_section(args, ws, rank, local, dev, dist):
     loop_ms = _timed_steps(loop, K, W, stream, flush, dev, dist)
     clocks = sampler.stop()
     # end to end: host buffers through the C ABI (copies inside the timed region)
-    src_h, dst_h = torch.from_numpy(src_np).pin_memory(), torch.from_numpy(dst_np).pin_memory()
-    sup_h = torch.empty(rows, dtype=torch.int32).pin_memory()
-    tr_h = torch.empty(rows, dtype=torch.int32).pin_memory()
-    km_h = torch.empty(G, dtype=torch.int32).pin_memory()
     e2e_ms = _timed_steps(
         lambda: ctx.decompose_batch(ns, off, src_h, dst_h, sup_h, tr_h, km_h, stream=stream),
         K, 1, stream, flush, dev, dist)
@@ -688,6 +688,14 @@ def run_single(args, ws, rank, local):
         n, src_np, dst_np = load_rows(wl)
         workload = WORKLOADS[wl]
     rows = len(src_np)
+    # pinned host buffers of the e2e leg, allocated before any device work
+    # (like a serving process that keeps its staging buffers): on this machine,
+    # pinned memory allocated after the 200 GB workspace copied at a tenth
+    # of the link's rate, torch's own copies included
+    src_h = torch.from_numpy(src_np).pin_memory()
+    dst_h = torch.from_numpy(dst_np).pin_memory()
+    sup_h = torch.empty(rows, dtype=torch.int32).pin_memory()
+    tr_h = torch.empty(rows, dtype=torch.int32).pin_memory()
     src = torch.from_numpy(src_np).to(dev)
     dst = torch.from_numpy(dst_np).to(dev)
     sup = torch.empty_like(src)
@@ -727,11 +735,7 @@ def run_single(args, ws, rank, local):
     m = st["m"]
     value = ws * m * args.steps / (total_ms / 1e3)
 
-    # end to end through the C ABI with pinned host buffers
-    src_h = torch.from_numpy(src_np).pin_memory()
-    dst_h = torch.from_numpy(dst_np).pin_memory()
-    sup_h = torch.empty(rows, dtype=torch.int32).pin_memory()
-    tr_h = torch.empty(rows, dtype=torch.int32).pin_memory()
+    # end to end through the C ABI with the pinned host buffers
     e2e_stage = {"build": [], "support": [], "lists": [], "peel": [], "scatter": []}
     e2e_layout = []
 
@@ -856,9 +860,9 @@ def main():
     ap.add_argument("--window", type=float, default=60.0, help="serve: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
     ap.add_argument("--serve-streams", type=int, default=4, help="serve: worker streams")
-    ap.add_argument("--serve-queue", type=int, default=64,
+    ap.add_argument("--serve-queue", type=int, default=16,
                     help="serve: waiting requests before submit is refused")
-    ap.add_argument("--serve-lead", type=float, default=0.25,
+    ap.add_argument("--serve-lead", type=float, default=1.0,
                     help="serve: seconds before its arrival a request is generated")
     args = ap.parse_args()
     if args.batch_steps <= 0:
