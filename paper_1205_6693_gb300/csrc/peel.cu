@@ -21,15 +21,17 @@
 //        frontier (warp-aggregated append).  F edges get truss number k.
 //
 // Load balance inside a sub-round (its time is that of the slowest warp):
-// when an edge joins a frontier it is expanded into work items of kItem list
-// entries each (at least one item, which also records its truss number); an
+// an edge that joins a frontier is staged by the warp that pushed it and
+// expanded, when that warp flushes, into work items of kItem list entries
+// each (at least one item, which also records its truss number); an
 // item carries its edge, its entry count and the offset of its entries, so a
 // warp goes from the item straight to the list.  Every warp takes 4 items per
 // iteration, 8 lanes per item and 2 entries per lane (independent loads in
 // flight).  A warp's share of a sub-round is then at most
 // ceil(items / (4 * warps)) iterations, whatever the lengths of the lists.
 // Appends are staged per warp in shared memory and flushed with one atomic
-// reservation per buffer, and per-level reductions (minimum residual, alive
+// reservation per buffer (the list lengths and offsets of a buffer's pushed
+// edges are loaded together at the flush), and per-level reductions (minimum residual, alive
 // count) are combined per block first: a single global counter hit by every
 // warp would serialise the whole grid on one L2 address.
 // Every scan and every sub-round is one phase, ended by one grid barrier.
@@ -68,7 +70,7 @@ namespace {
 constexpr int kPeelBlock = 512;
 constexpr int kWarps = kPeelBlock / 32;
 constexpr int kItem = 16;  // list entries per work item (8 lanes x 2)
-constexpr int kWQ = 64;    // work items staged per warp
+constexpr int kWP = 32;    // pushed edges staged per warp (one per lane)
 constexpr int kWA = 128;   // alive-list entries staged per warp
 
 struct PeelCtl {
@@ -113,6 +115,14 @@ struct PeelArgs {
   int lvl_cap;
 };
 
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ int items_of(int len) { return len > 0 ? (len + kItem - 1) / kItem : 1; }
 
 constexpr int kTagMod = 65534;
@@ -137,24 +147,55 @@ __device__ __forceinline__ int4 make_item(int e, int na, int nb, bool first, int
 
 // Per-warp staging buffers in shared memory (counts are warp-uniform).
 struct WarpBuf {
-  int4 *items;
-  int ni;
+  int32_t *push;  // edges pushed to the next frontier, not yet expanded
+  int np;
   int32_t *alive;
   int na;
 };
 
-// Write the staged items to queue Q with one reservation.
-__device__ __forceinline__ void flush_items(const PeelArgs &a, WarpBuf &wb, int4 *Q,
-                                            unsigned long long *qctr) {
-  if (wb.ni == 0) return;
+// Expand the staged pushed edges into work items and append them to queue Q
+// with one reservation.  The list length and offsets of all staged edges
+// are loaded together here, once per flush, instead of one dependent round
+// trip per push inside the sub-round's loop.
+template <bool OWN>
+__device__ __forceinline__ void flush_push(const PeelArgs &a, WarpBuf &wb, int4 *Q,
+                                           unsigned long long *qctr) {
+  const int np = wb.np;
+  if (np == 0) return;
   const int lane = lane_id();
+  const bool v = lane < np;
+  const int p = v ? wb.push[lane] : 0;
+  const int L = v ? __ldg(&a.sup[p]) : 0;
+  const int64_t lb = v ? __ldg(&a.off[p]) : 0;
+  const int cA = (OWN && v) ? __ldg(&a.own_cnt[p]) : 0;
+  const int64_t la = (OWN && v) ? __ldg(&a.own_off[p]) : 0;
+  const int n = v ? items_of(L) : 0;
+  const int P = warp_incl_scan(n);
+  const int tot = __shfl_sync(TR_FULL, P, 31);
   unsigned long long b = 0;
-  if (lane == 0) b = atomicAdd(qctr, (unsigned long long)wb.ni);
-  const long long b0 = (long long)__shfl_sync(TR_FULL, b, 0);
-  for (int t = lane; t < wb.ni; t += 32)
-    if (b0 + t < a.item_cap) Q[b0 + t] = wb.items[t];
+  if (lane == 0) b = atomicAdd(qctr, (unsigned long long)tot);
+  const long long base = (long long)__shfl_sync(TR_FULL, b, 0);
+  for (int u0 = 0; u0 < tot; u0 += 32) {
+    const int t = u0 + lane;
+    const int o = warp_owner(P, t < tot ? t : tot - 1);
+    const int po = __shfl_sync(TR_FULL, p, o);
+    const int Po = __shfl_sync(TR_FULL, P, o);
+    const int no = __shfl_sync(TR_FULL, n, o);
+    const int Lo = __shfl_sync(TR_FULL, L, o);
+    const int cAo = OWN ? __shfl_sync(TR_FULL, cA, o) : 0;
+    const int64_t lao = OWN ? __shfl_sync(TR_FULL, la, o) : 0;
+    const int64_t lbo = __shfl_sync(TR_FULL, lb, o);
+    const long long idx = base + t;
+    if (t < tot && idx < a.item_cap) {
+      const int it = t - (Po - no);
+      const int start = it * kItem;
+      const int cnt = Lo > 0 ? min(kItem, Lo - start) : 0;
+      const int na = min(max(cAo - start, 0), cnt);
+      Q[idx] = make_item(po, na, cnt - na, it == 0, lao + start, lbo + max(start - cAo, 0));
+    }
+  }
   __syncwarp();
-  wb.ni = 0;
+  wb.np = 0;
 }
 
 __device__ __forceinline__ void flush_alive(const PeelArgs &a, WarpBuf &wb, int32_t *A2,
@@ -182,64 +223,29 @@ __device__ __forceinline__ void push_alive(const PeelArgs &a, bool keep, int e, 
   wb.na += tot;
 }
 
-// Append the work items of edge p (for each lane with `push`) to queue Q,
-// stamping p with tag `tagv`.  All lanes call it.  Small batches go through
-// the warp's staging buffer; a batch larger than the buffer is written
-// straight to Q with its own reservation.
+// Push edge p (for each lane with `push`) to the next frontier: stamp it
+// with tag `tagv` and stage it for expansion into work items.  All lanes
+// call it.
 template <bool OWN>
 __device__ __forceinline__ void push_items(const PeelArgs &a, bool push, int p, WarpBuf &wb,
                                            int4 *Q, unsigned long long *qctr, uint16_t tagv) {
-  const int lane = lane_id();
-  int n = 0, L = 0, cA = 0;
-  int64_t la = 0, lb = 0;
+  const unsigned mask = __ballot_sync(TR_FULL, push);
+  if (mask == 0) return;
+  const int tot = __popc(mask);
+  if (wb.np + tot > kWP) flush_push<OWN>(a, wb, Q, qctr);
   if (push) {
-    L = __ldg(&a.sup[p]);
-    lb = __ldg(&a.off[p]);
-    if (OWN) {
-      cA = __ldg(&a.own_cnt[p]);
-      la = __ldg(&a.own_off[p]);
-    }
-    n = items_of(L);
     a.stamp[p] = tagv;
-  }
-  const int P = warp_incl_scan(n);
-  const int tot = __shfl_sync(TR_FULL, P, 31);
-  if (tot == 0) return;
-  int4 *dst;
-  long long b0;
-  if (tot > kWQ) {
-    unsigned long long b = 0;
-    if (lane == 31) b = atomicAdd(qctr, (unsigned long long)tot);
-    b0 = (long long)__shfl_sync(TR_FULL, b, 31);
-    dst = Q;
-  } else {
-    if (wb.ni + tot > kWQ) flush_items(a, wb, Q, qctr);
-    b0 = wb.ni;
-    dst = wb.items;
-  }
-  const long long lim = tot > kWQ ? a.item_cap : (long long)kWQ;
-  for (int t0 = 0; t0 < tot; t0 += 32) {
-    const int t = t0 + lane;
-    const int o = warp_owner(P, t < tot ? t : tot - 1);
-    const int po = __shfl_sync(TR_FULL, p, o);
-    const int Po = __shfl_sync(TR_FULL, P, o);
-    const int no = __shfl_sync(TR_FULL, n, o);
-    const int Lo = __shfl_sync(TR_FULL, L, o);
-    const int cAo = OWN ? __shfl_sync(TR_FULL, cA, o) : 0;
-    const int64_t lao = OWN ? __shfl_sync(TR_FULL, la, o) : 0;
-    const int64_t lbo = __shfl_sync(TR_FULL, lb, o);
-    const long long idx = b0 + t;
-    if (t < tot && idx < lim) {
-      const int it = t - (Po - no);
-      const int start = it * kItem;
-      const int cnt = Lo > 0 ? min(kItem, Lo - start) : 0;
-      const int na = min(max(cAo - start, 0), cnt);
-      dst[idx] = make_item(po, na, cnt - na, it == 0, lao + start,
-                           lbo + max(start - cAo, 0));
+    wb.push[wb.np + __popc(mask & ((1u << lane_id()) - 1u))] = p;
+    // the flush reads p's list length and offsets: start fetching them now
+    prefetch_l1(a.sup + p);
+    prefetch_l1(a.off + p);
+    if (OWN) {
+      prefetch_l1(a.own_cnt + p);
+      prefetch_l1(a.own_off + p);
     }
   }
   __syncwarp();
-  if (tot <= kWQ) wb.ni += tot;
+  wb.np += tot;
 }
 
 // Decide whether frontier edge e charges the triangle {e, p1, p2} in
@@ -341,10 +347,10 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
   const int twarps = gridDim.x * kWarps;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   PeelCtl *ctl = a.ctl;
-  __shared__ int4 s_items[kWarps][kWQ];
+  __shared__ int32_t s_push[kWarps][kWP];
   __shared__ int32_t s_alive[kWarps][kWA];
   __shared__ int s_minres, s_live;
-  WarpBuf wb{s_items[wib], 0, s_alive[wib], 0};
+  WarpBuf wb{s_push[wib], 0, s_alive[wib], 0};
   if (threadIdx.x == 0) {
     s_minres = INT_MAX;
     s_live = 0;
@@ -445,7 +451,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         push_items<OWN>(a, has, q, wb, F, qf, tag_of(s));
       }
     }
-    flush_items(a, wb, F, qf);
+    flush_push<OWN>(a, wb, F, qf);
     if (compact) flush_alive(a, wb, alive2, qa);
     if (lane == 0) {
       if (wmin != INT_MAX) atomicMin(&s_minres, wmin);
@@ -495,7 +501,17 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
         ctl->qa[(ph + 1) % 3] = 0;
       }
       const int grp = lane >> 3, j = lane & 7;
-      for (int64_t base = (int64_t)gwarp * 4 * G; base < nCur; base += (int64_t)twarps * 4 * G) {
+      const int64_t stride = (int64_t)twarps * 4 * G;
+      for (int64_t base = (int64_t)gwarp * 4 * G; base < nCur; base += stride) {
+        // this iteration's items were loaded one iteration ahead (the first
+        // right after the barrier); load the next iteration's now
+        int4 cur[G];
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          cur[g] = pre[g];
+          const int64_t nx = base + stride + g * 4 + grp;
+          pre[g] = nx < nCur ? __ldcg(&F[nx]) : make_int4(0, 0, 0, 0);
+        }
         int ee[2 * G];
         bool vv[2 * G];
         int2 pp[2 * G];
@@ -510,7 +526,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           la[g] = 0;
           lb[g] = 0;
           if (it < nCur) {
-            const int4 item = base == (int64_t)gwarp * 4 * G ? pre[g] : __ldcg(&F[it]);
+            const int4 item = cur[g];
             const uint32_t hi = (uint32_t)item.y;
             ee[2 * g] = item.x;
             na[g] = OWN ? (int)(hi & 31u) : 0;
@@ -545,10 +561,26 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
           vv[2 * g + 1] = vv[2 * g + 1] && r[g] > 0;
           n_entries += (unsigned)(vv[2 * g] + vv[2 * g + 1]);
         }
+        // the next iteration's items have arrived by now: start fetching
+        // their list entries (into L1; the lists are read-only here) and
+        // their edges' residuals (into L2) while this iteration charges
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          const uint32_t hi = (uint32_t)pre[g].y;
+          const int nna = OWN ? (int)(hi & 31u) : 0;
+          const int ncnt = nna + (int)((hi >> 5) & 31u);
+          const int64_t nla =
+              OWN ? (int64_t)(((uint64_t)((hi >> 11) & 0x3FFu) << 32) | (uint32_t)pre[g].z) : 0;
+          const int64_t nlb = (int64_t)(((uint64_t)(hi >> 21) << 32) | (uint32_t)pre[g].w);
+          if (j < ncnt) prefetch_l1(j < nna ? a.own + nla + j : a.rest + nlb + (j - nna));
+          if (j + 8 < ncnt)
+            prefetch_l1(j + 8 < nna ? a.own + nla + j + 8 : a.rest + nlb + (j + 8 - nna));
+          if (j == 0 && ncnt > 0) prefetch_l2(a.res + pre[g].x);
+        }
         charge<2 * G, OWN, COUNT>(a, ee, vv, pp, k, ts, tn, wb, N, qn, n_dec, s_lvl0, n_dead,
                                   n_early);
       }
-      flush_items(a, wb, N, qn);
+      flush_push<OWN>(a, wb, N, qn);
       if (COUNT && k < a.lvl_cap) {
         unsigned x0 = n_entries - c_ent, x1 = n_dead - c_dead, x2 = n_early - c_early;
         for (int o = 16; o >= 1; o >>= 1) {

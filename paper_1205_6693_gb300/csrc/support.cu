@@ -50,6 +50,7 @@ struct ListArgs {
   const int32_t *adjp;
   const int32_t *esrc;
   const int64_t *wpre;  // [m+1] exclusive prefix of the owner-centric walk cost
+  const int64_t *rb;    // [P+1] range r = edges [rb[r], rb[r+1])
   int64_t W;            // total walk cost
   int64_t P;            // number of ranges
   int stage_max;        // stage out(u) in shared memory when |out(u)| <= this
@@ -59,6 +60,11 @@ struct ListArgs {
   int64_t entries;      // size of pairs (writes beyond it are dropped)
   int *err;             // set to TRUSS_ECHECK if a list would overflow
 };
+
+// r W / P without overflowing 64 bits (r <= P <= m).
+__device__ __forceinline__ int64_t range_point(int64_t W, int64_t P, int64_t r) {
+  return (W / P) * r + (W % P) * r / P;
+}
 
 // First e in [0, m] with wpre[e] >= x.
 __device__ __forceinline__ int64_t lower_bound64(const int64_t *a, int64_t m, int64_t x) {
@@ -205,8 +211,11 @@ struct SupVArgs {
   const int32_t *inedge;  // [m] edges grouped by head
   const int32_t *ihead;   // [m] head of inedge[i]
   const int64_t *inoff;   // [n+1] start of each head's group
+  const int64_t *wcost;   // [m] walk cost of inedge[i]: |out(u) after v| + ecost
   const int64_t *wpre;    // [m+1] exclusive prefix of the walk cost, in inedge order
+  const int64_t *rb;      // [P+1] range r = inedge positions [rb[r], rb[r+1])
   int64_t W, P;
+  int ecost;      // the fixed part of wcost
   int stage_min;  // out-lists shorter than this are searched in global memory
   int stage_max;  // out-lists staged with their counts up to this many entries
   int hash_max;   // longer ones get a shared table of positions up to this many
@@ -275,10 +284,10 @@ __device__ __forceinline__ void head_walk(const SupVArgs &a, int64_t i0, int64_t
   for (int64_t c0 = i0; c0 < i1; c0 += 32) {
     const int64_t j = c0 + lane;
     const bool valid = j < i1;
+    // the walk length comes with the edge (its cost, by position), not from
+    // the tail's offsets: two dependent loads fewer before the walk starts
     const int e = valid ? __ldg(&a.inedge[j]) : 0;
-    const int u = valid ? __ldg(&a.esrc[e]) : 0;
-    const int64_t uend = valid ? __ldg(&a.offp[u + 1]) : 0;
-    const int len = valid ? (int)(uend - (int64_t)e - 1) : 0;  // entries of out(u) after v
+    const int len = valid ? (int)(__ldg(&a.wcost[j]) - a.ecost) : 0;  // out(u) after v
     const int64_t rb = (valid && a.tb) ? __ldg(&a.tbpre[e]) : 0;
 
     // short walks, flattened: step t of the warp is entry t - base(o) of
@@ -384,8 +393,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_support_v(SupVArgs a) {
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = gw; r < a.P; r += nw) {
-    const int64_t ia = lower_bound64(a.wpre, a.m, a.W * r / a.P);
-    const int64_t ib = lower_bound64(a.wpre, a.m, a.W * (r + 1) / a.P);
+    const int64_t ia = __ldg(&a.rb[r]), ib = __ldg(&a.rb[r + 1]);
     int64_t i = ia;
     while (i < ib) {
       const int v = __ldg(&a.ihead[i]);
@@ -502,8 +510,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_list_walk(ListArgs a) {
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = gw; r < a.P; r += nw) {
-    const int64_t ea = lower_bound64(a.wpre, a.m, a.W * r / a.P);
-    const int64_t eb = lower_bound64(a.wpre, a.m, a.W * (r + 1) / a.P);
+    const int64_t ea = __ldg(&a.rb[r]), eb = __ldg(&a.rb[r + 1]);
     int64_t e = ea;
     while (e < eb) {
       const int u = __ldg(&a.esrc[e]);
@@ -795,8 +802,18 @@ __global__ void k_cursors(int64_t m, const int64_t *toff, const int32_t *supA,
   }
 }
 
+// rb[r] = first position whose walk-cost prefix reaches r W / P, for
+// r = 0 .. P: one search per range here instead of two dependent chains of
+// ~log2(m) loads at the start of every range in a walk.
+__global__ void k_range_bounds(int64_t m, int64_t P, int64_t W, const int64_t *wpre,
+                               int64_t *rb) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= P;
+       r += (int64_t)gridDim.x * blockDim.x)
+    rb[r] = lower_bound64(wpre, m, range_point(W, P, r));
+}
+
 // The owner-centric list walk, used when the triangle records do not fit.
-int launch_list_walk(ListArgs a, const SupportCfg &cfg, cudaStream_t s) {
+int launch_list_walk(Arena &A, ListArgs a, const SupportCfg &cfg, cudaStream_t s) {
   int dev = 0, sms = cfg.sms;
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -814,13 +831,18 @@ int launch_list_walk(ListArgs a, const SupportCfg &cfg, cudaStream_t s) {
   if (P < warps) P = warps;
   if (P > a.m) P = a.m > 0 ? a.m : 1;
   a.P = P;
+  int64_t *rb = A.get<int64_t>(P + 1);
+  if (!rb) return TRUSS_ENOMEM;
+  k_range_bounds<<<grid_for(P + 1, 256, 152 * 8), 256, 0, s>>>(a.m, P, a.W, a.wpre, rb);
+  TR_LAUNCHED();
+  a.rb = rb;
   a.stage_max = cfg.stage_max > 0 && cfg.stage_max < kListCap ? cfg.stage_max : kListCap;
   k_list_walk<<<grid, kBlock, smem, s>>>(a);
   TR_LAUNCHED();
   return TRUSS_OK;
 }
 
-int launch_walk_v(SupVArgs a, const SupportCfg &cfg, cudaStream_t s) {
+int launch_walk_v(Arena &A, SupVArgs a, const SupportCfg &cfg, cudaStream_t s) {
   int dev = 0, sms = cfg.sms;
   TR_CUDA(cudaGetDevice(&dev));
   if (sms <= 0) TR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -836,6 +858,11 @@ int launch_walk_v(SupVArgs a, const SupportCfg &cfg, cudaStream_t s) {
   if (P < warps) P = warps;
   if (P > a.m) P = a.m > 0 ? a.m : 1;
   a.P = P;
+  int64_t *rb = A.get<int64_t>(P + 1);
+  if (!rb) return TRUSS_ENOMEM;
+  k_range_bounds<<<grid_for(P + 1, 256, 152 * 8), 256, 0, s>>>(a.m, P, a.W, a.wpre, rb);
+  TR_LAUNCHED();
+  a.rb = rb;
   a.stage_max = cfg.stage_max > 0 && cfg.stage_max < kHeadCap ? cfg.stage_max : kHeadCap;
   a.hash_max = kHashOnlyCap;
   a.stage_min = kStageMin;
@@ -936,14 +963,16 @@ int run_support(Arena &A, const Csr &g, const SupportCfg &cfg, SupportOut *out, 
     a.inedge = inedge;
     a.ihead = ihead;
     a.inoff = inoff;
+    a.wcost = wcost;
     a.wpre = wpre;
     a.W = W;
+    a.ecost = cfg.pair_cost > 0 ? cfg.pair_cost : cfg.pair_cost < 0 ? 0 : kEdgeCost;
     a.supA = supA;
     a.supB = supB;
     a.tbpre = tbpre;
     a.tb = recs;
     a.cuv = cuv;
-    TR_TRY(launch_walk_v(a, cfg, s));
+    TR_TRY(launch_walk_v(A, a, cfg, s));
   }
   k_sum<<<grid_for(m + 1, 256, 152 * 16), 256, 0, s>>>(m, supA, supB, sup, sup64);
   TR_LAUNCHED();
@@ -1124,7 +1153,7 @@ int run_lists(Arena &A, const Csr &g, const SupportCfg &cfg, const SupportOut &s
   a.pairs = pairs;
   a.entries = so.entries;
   a.err = err;
-  TR_TRY(launch_list_walk(a, cfg, s));
+  TR_TRY(launch_list_walk(A, a, cfg, s));
   int h_err = 0;
   TR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   TR_CUDA(cudaStreamSynchronize(s));
