@@ -13,7 +13,9 @@ mid`` times the R-MAT scale-20 graph instead.
 Prints ONE JSON line (rank 0).  `value` is distinct edges decomposed per
 second summed over ranks (each rank decomposes its own replica: one graph does
 not shard).  `e2e` is the same metric through the C ABI with pinned host
-buffers, host<->device copies inside the timed region.  `roofline` reports
+buffers: moving the rows to the GPU and the outputs back is inside the timed
+region (the library's kernels read and write pinned buffers in place over
+the host link; the byte counts are those moved).  `roofline` reports
 the dominant kernel's algorithmic bytes (the per-edge formulas that
 truss_run_stats documents) over its CUDA-event duration against the measured
 HBM copy bandwidth, with the kernel's bytes by its own per-unit figures

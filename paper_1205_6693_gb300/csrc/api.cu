@@ -243,11 +243,34 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device address of pinned (page-locked) host memory, or nullptr for any
+// other memory.  Kernels can read and write pinned memory in place over the
+// host link (NVLink-C2C on Grace machines), which moves each byte once and
+// needs no staging buffer.
+void *pinned_view(const void *p) {
+  cudaPointerAttributes at{};
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Device-usable input: device memory as is; with `direct`, pinned host
+// memory in place (for inputs one kernel reads once); otherwise a staged
+// copy in the arena.
 template <class T>
-int stage_in(tr::Arena &A, const T *p, int64_t count, const T **out, cudaStream_t s) {
+int stage_in(tr::Arena &A, const T *p, int64_t count, const T **out, cudaStream_t s,
+             bool direct = false) {
   if (count == 0 || p == nullptr || is_device_ptr(p)) {
     *out = p;
     return TRUSS_OK;
+  }
+  if (direct) {
+    if (const void *dp = pinned_view(p)) {
+      *out = (const T *)dp;
+      return TRUSS_OK;
+    }
   }
   T *d = A.get<T>(count);
   if (!d) return TRUSS_ENOMEM;
@@ -262,12 +285,20 @@ struct OutBuf {
   bool host = false;
 };
 
-int stage_out(tr::Arena &A, int32_t *user, int64_t count, OutBuf *o) {
+// Device-usable output: device memory as is; with `direct`, pinned host
+// memory written in place; otherwise an arena buffer copied back.
+int stage_out(tr::Arena &A, int32_t *user, int64_t count, OutBuf *o, bool direct = false) {
   o->user = user;
   o->host = false;
   o->dev = user;
   if (!user) return TRUSS_OK;
   if (!is_device_ptr(user)) {
+    if (direct) {
+      if (void *dp = pinned_view(user)) {
+        o->dev = (int32_t *)dp;
+        return TRUSS_OK;
+      }
+    }
     o->host = true;
     o->dev = A.get<int32_t>(count);
     if (!o->dev) return TRUSS_ENOMEM;
@@ -313,8 +344,9 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   tr::RowsIn in;
   in.rows = rows;
   in.n = n_total;
-  TR_TRY(stage_in(A, src, rows, &in.src, s));
-  TR_TRY(stage_in(A, dst, rows, &in.dst, s));
+  // the rows are read once, by the key kernel: pinned host rows in place
+  TR_TRY(stage_in(A, src, rows, &in.src, s, true));
+  TR_TRY(stage_in(A, dst, rows, &in.dst, s, true));
   int64_t *d_row_off = nullptr, *d_voff = nullptr;
   if (h_row_off) {
     d_row_off = A.get<int64_t>(G + 1);
@@ -396,9 +428,11 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
     st.peel_scanned = (int64_t)pr.scanned;
   }
 
+  // the per-row outputs are written once, by the scatter: pinned host
+  // outputs in place
   OutBuf os, ot;
-  TR_TRY(stage_out(A, support_out, rows, &os));
-  TR_TRY(stage_out(A, want_truss ? truss_out : nullptr, rows, &ot));
+  TR_TRY(stage_out(A, support_out, rows, &os, true));
+  TR_TRY(stage_out(A, want_truss ? truss_out : nullptr, rows, &ot, true));
   TR_TRY(tr::scatter_rows(g, so.sup, truss_e, os.dev, ot.dev, s));
   if (G > 1 || h_row_off) {
     if (kmax_out && want_truss) {

@@ -117,6 +117,30 @@ def test_host_pointers_match_device(ctx):
     assert kmax == ref.kmax
 
 
+def test_pinned_host_buffers_match_oracle(ctx):
+    # pinned (page-locked) rows and outputs are read and written in place by
+    # the kernels; pageable ones go through staged copies; mixing the kinds
+    # in one call must not matter
+    n, (src, dst) = 2 ** 13, graphgen.rmat_raw(13, 16 * 2 ** 13, seed=7)
+    ref = oracle.truss(n, src, dst)
+    s = torch.from_numpy(np.ascontiguousarray(src, np.int32)).pin_memory()
+    d = torch.from_numpy(np.ascontiguousarray(dst, np.int32)).pin_memory()
+    sup = torch.full_like(s, -7).pin_memory()
+    tr = torch.full_like(s, -7).pin_memory()
+    kmax = ctx.decompose(n, s, d, sup, tr)
+    assert np.array_equal(sup.numpy(), ref.support) and np.array_equal(tr.numpy(), ref.truss)
+    assert kmax == ref.kmax
+    dev = torch.device("cuda:0")
+    sup2 = np.full(len(src), -7, np.int32)  # pageable output
+    tr2 = torch.full((len(src),), -7, dtype=torch.int32, device=dev)  # device output
+    ctx.decompose(n, s, np.ascontiguousarray(dst, np.int32), sup2, tr2)
+    assert np.array_equal(sup2, ref.support)
+    assert np.array_equal(tr2.cpu().numpy(), ref.truss)
+    sup3 = torch.full_like(s, -7).pin_memory()
+    ctx.support(n, s, d, sup3)
+    assert np.array_equal(sup3.numpy(), ref.support)
+
+
 def test_support_only(ctx):
     n, (src, dst) = 4096, graphgen.rmat_raw(12, 16 * 4096, seed=5)
     ref = oracle.truss(n, src, dst, with_truss=False)
