@@ -63,19 +63,19 @@ __global__ void k_run_heads(int64_t rows, const uint64_t *sk, uint64_t sentinel,
   }
 }
 
-__global__ void k_lex_edges(int64_t rows, const uint64_t *sk, const int32_t *srow,
-                            const int32_t *runid, uint64_t sentinel, int b, int32_t *U, int32_t *V,
-                            int32_t *rowlex) {
+// Distinct edges in lexicographic order (U, V) from the sorted row keys;
+// runid[i] becomes the 1-based edge id of sorted row i, 0 for a self-loop.
+__global__ void k_lex_edges(int64_t rows, const uint64_t *sk, int32_t *runid, uint64_t sentinel,
+                            int b, int32_t *U, int32_t *V) {
   const uint64_t mask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
        i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t k = sk[i];
     if (k == sentinel) {
-      rowlex[srow[i]] = -1;
+      runid[i] = 0;
       continue;
     }
     int32_t id = runid[i] - 1;
-    rowlex[srow[i]] = id;
     if (i == 0 || sk[i - 1] != k) {
       U[id] = (int32_t)(k >> b);
       V[id] = (int32_t)(k & mask);
@@ -125,6 +125,9 @@ __global__ void k_orient_keys(int64_t m, const int32_t *U, const int32_t *V, con
   }
 }
 
+// The oriented edges are sorted by tail, so each run of equal tails adds
+// its length to outdeg once: minus its first index at its first edge, its
+// end at its last.
 __global__ void k_oriented(int64_t m, const uint64_t *ok, const int32_t *olex, int b,
                            int32_t *adjp, int32_t *esrc, int32_t *lex2e, int64_t *outdeg) {
   const uint64_t mask = (1ull << b) - 1;
@@ -135,15 +138,22 @@ __global__ void k_oriented(int64_t m, const uint64_t *ok, const int32_t *olex, i
     adjp[p] = y;
     esrc[p] = x;
     lex2e[olex[p]] = (int32_t)p;
-    atomicAdd((unsigned long long *)&outdeg[x], 1ull);
+    if (p == 0 || (int32_t)(ok[p - 1] >> b) != x)
+      atomicAdd((unsigned long long *)&outdeg[x], (unsigned long long)(-p));
+    if (p + 1 == m || (int32_t)(ok[p + 1] >> b) != x)
+      atomicAdd((unsigned long long *)&outdeg[x], (unsigned long long)(p + 1));
   }
 }
 
-__global__ void k_row2e(int64_t rows, const int32_t *rowlex, const int32_t *lex2e, int32_t *row2e) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    int32_t l = rowlex[r];
-    row2e[r] = l < 0 ? -1 : lex2e[l];
+// Row srow[i] (sorted row i) -> its canonical edge: the lexicographic id is
+// runid[i] - 1 (0: a self-loop), read in order, so lex2e is read in order
+// and only the write to row2e lands at random.
+__global__ void k_row2e(int64_t rows, const int32_t *srow, const int32_t *runid,
+                        const int32_t *lex2e, int32_t *row2e) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = runid[i];
+    row2e[srow[i]] = l > 0 ? lex2e[l - 1] : -1;
   }
 }
 
@@ -183,8 +193,7 @@ int build_csr(Arena &A, const RowsIn &in, Csr *out, int32_t *d_err, cudaStream_t
   uint64_t *keys = A.get<uint64_t>(rows), *skeys = A.get<uint64_t>(rows);
   int32_t *vals = A.get<int32_t>(rows), *srow = A.get<int32_t>(rows);
   int32_t *flag = A.get<int32_t>(rows), *runid = A.get<int32_t>(rows);
-  int32_t *rowlex = A.get<int32_t>(rows);
-  if (!keys || !skeys || !vals || !srow || !flag || !runid || !rowlex) return TRUSS_ENOMEM;
+  if (!keys || !skeys || !vals || !srow || !flag || !runid) return TRUSS_ENOMEM;
   k_make_keys<<<grid_for(rows, kBlock, maxg), kBlock, 0, s>>>(in, b, sentinel, keys, vals, d_err);
   TR_LAUNCHED();
   size_t tb = 0;
@@ -210,8 +219,8 @@ int build_csr(Arena &A, const RowsIn &in, Csr *out, int32_t *d_err, cudaStream_t
   out->m = m;
   int32_t *U = A.get<int32_t>(m), *V = A.get<int32_t>(m);
   if (!U || !V) return TRUSS_ENOMEM;
-  k_lex_edges<<<grid_for(rows, kBlock, maxg), kBlock, 0, s>>>(rows, skeys, srow, runid, sentinel,
-                                                               b, U, V, rowlex);
+  k_lex_edges<<<grid_for(rows, kBlock, maxg), kBlock, 0, s>>>(rows, skeys, runid, sentinel, b, U,
+                                                               V);
   TR_LAUNCHED();
 
   // 3. degrees and rank
@@ -245,15 +254,17 @@ int build_csr(Arena &A, const RowsIn &in, Csr *out, int32_t *d_err, cudaStream_t
   out->esrc = esrc;
   TR_CUDA(cudaMemsetAsync(outdeg, 0, sizeof(int64_t) * (n + 1), s));
   if (m > 0) {
-    // reuse the row-sized key/value buffers (m <= rows)
+    // reuse the row-sized key/value buffers (m <= rows); srow and runid
+    // stay for the row -> edge map, flag (dead) takes the sorted values
+    int32_t *olex = flag;
     k_orient_keys<<<grid_for(m, kBlock, maxg), kBlock, 0, s>>>(m, U, V, newid, b, keys, vals);
     TR_LAUNCHED();
     tb = 0;
-    TR_TRY(sort_pairs_u64(nullptr, &tb, keys, skeys, vals, srow, m, 0, 2 * b, s));
+    TR_TRY(sort_pairs_u64(nullptr, &tb, keys, skeys, vals, olex, m, 0, 2 * b, s));
     tmp = A.alloc(tb);
     if (!tmp) return TRUSS_ENOMEM;
-    TR_TRY(sort_pairs_u64(tmp, &tb, keys, skeys, vals, srow, m, 0, 2 * b, s));
-    k_oriented<<<grid_for(m, kBlock, maxg), kBlock, 0, s>>>(m, skeys, srow, b, adjp, esrc, lex2e,
+    TR_TRY(sort_pairs_u64(tmp, &tb, keys, skeys, vals, olex, m, 0, 2 * b, s));
+    k_oriented<<<grid_for(m, kBlock, maxg), kBlock, 0, s>>>(m, skeys, olex, b, adjp, esrc, lex2e,
                                                              outdeg);
     TR_LAUNCHED();
   }
@@ -264,7 +275,7 @@ int build_csr(Arena &A, const RowsIn &in, Csr *out, int32_t *d_err, cudaStream_t
   TR_TRY(exclusive_sum_i64(tmp, &tb, outdeg, offp, n + 1, s));
 
   // 5. rows -> canonical edge ids
-  k_row2e<<<grid_for(rows, kBlock, maxg), kBlock, 0, s>>>(rows, rowlex, lex2e, row2e);
+  k_row2e<<<grid_for(rows, kBlock, maxg), kBlock, 0, s>>>(rows, srow, runid, lex2e, row2e);
   TR_LAUNCHED();
   return TRUSS_OK;
 }
