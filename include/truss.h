@@ -22,8 +22,11 @@
  *   must be < 2^31 (edge ids are int32).  n must be < 2^31.
  * - Every per-row output is indexed by input row and is int32.
  * - Pointers may be device memory or host memory (pageable or pinned); the
- *   library detects which with cudaPointerGetAttributes and stages host
- *   buffers through device memory it owns.  The caller owns every input and
+ *   library detects which with cudaPointerGetAttributes.  truss_support,
+ *   truss_decompose and truss_decompose_batch read pinned host rows and
+ *   write pinned host per-row outputs in place from their kernels (through
+ *   the memory's device address); every other host buffer is staged
+ *   through device memory the library owns.  The caller owns every input and
  *   output buffer; the library owns its workspace (a per-context arena that
  *   grows on demand and is released by truss_ctx_destroy).
  * - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Work
