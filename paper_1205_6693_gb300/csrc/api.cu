@@ -164,6 +164,25 @@ __global__ void k_scatter(int64_t rows, const int32_t *row2e, const int32_t *sup
   }
 }
 
+// Support and truss number of each edge side by side, so that the per-row
+// scatter gathers one 8-byte pair per row instead of two scattered words.
+__global__ void k_pack(int64_t m, const int32_t *sup, const int32_t *truss, int2 *pk) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    pk[e] = make_int2(sup[e], truss[e]);
+}
+
+__global__ void k_scatter_pk(int64_t rows, const int32_t *row2e, const int2 *pk,
+                             int32_t *sup_rows, int32_t *truss_rows) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = row2e[r];
+    const int2 v = e < 0 ? make_int2(-1, -1) : pk[e];
+    sup_rows[r] = v.x;
+    truss_rows[r] = v.y;
+  }
+}
+
 // One block per graph: k_max = max truss number over its rows.
 __global__ void k_batch_kmax(int32_t G, const int64_t *row_off, const int32_t *truss_rows,
                              int32_t *kmax) {
@@ -216,6 +235,18 @@ int scatter_rows(const Csr &g, const int32_t *sup, const int32_t *truss, int32_t
   if (g.rows == 0) return TRUSS_OK;
   k_scatter<<<grid_for(g.rows, 256, 152 * 16), 256, 0, s>>>(g.rows, g.row2e, sup, truss, sup_rows,
                                                              truss_rows);
+  TR_LAUNCHED();
+  return TRUSS_OK;
+}
+
+int scatter_rows_packed(Arena &A, const Csr &g, const int32_t *sup, const int32_t *truss,
+                        int32_t *sup_rows, int32_t *truss_rows, cudaStream_t s) {
+  int2 *pk = (sup_rows && truss_rows && g.m > 0) ? A.get<int2>(g.m) : nullptr;
+  if (!pk) return scatter_rows(g, sup, truss, sup_rows, truss_rows, s);
+  k_pack<<<grid_for(g.m, 256, 152 * 16), 256, 0, s>>>(g.m, sup, truss, pk);
+  TR_LAUNCHED();
+  k_scatter_pk<<<grid_for(g.rows, 256, 152 * 16), 256, 0, s>>>(g.rows, g.row2e, pk, sup_rows,
+                                                                truss_rows);
   TR_LAUNCHED();
   return TRUSS_OK;
 }
@@ -433,7 +464,7 @@ int run_pipeline(truss_ctx *ctx, int64_t n_total, int64_t rows, const int32_t *s
   OutBuf os, ot;
   TR_TRY(stage_out(A, support_out, rows, &os, true));
   TR_TRY(stage_out(A, want_truss ? truss_out : nullptr, rows, &ot, true));
-  TR_TRY(tr::scatter_rows(g, so.sup, truss_e, os.dev, ot.dev, s));
+  TR_TRY(tr::scatter_rows_packed(A, g, so.sup, truss_e, os.dev, ot.dev, s));
   if (G > 1 || h_row_off) {
     if (kmax_out && want_truss) {
       OutBuf ok;

@@ -210,6 +210,10 @@ int count_min_alive(Arena &A, const Csr &g, const SupportOut &so, const int32_t 
 // -------------------------------------------------------------- outputs ---
 int scatter_rows(const Csr &g, const int32_t *sup, const int32_t *truss, int32_t *sup_rows,
                  int32_t *truss_rows, cudaStream_t s);
+// The same through a packed (support, truss) pair per edge when both outputs
+// are wanted and the workspace has room for it.
+int scatter_rows_packed(Arena &A, const Csr &g, const int32_t *sup, const int32_t *truss,
+                        int32_t *sup_rows, int32_t *truss_rows, cudaStream_t s);
 int batch_kmax(int32_t G, const int64_t *row_off, const int32_t *truss_rows, int32_t *kmax,
                cudaStream_t s);
 // Per-graph distinct edges and support sums of a batch (voff: device vertex
