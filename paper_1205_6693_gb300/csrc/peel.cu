@@ -12,7 +12,7 @@
 //  scan (per level k):  F = {alive e : res[e] <= k-2}; the minimum residual
 //        of the other alive edges is taken, so an empty level jumps straight
 //        to k = min res + 2.  The list of alive edges scanned is rewritten
-//        without the removed ones once at least an eighth of it is dead.
+//        without the removed ones once at least a quarter of it is dead.
 //  sub-round:  for every e in F and every triangle {e, e1, e2} on e's list
 //        whose edges are all still alive, the triangle is charged exactly
 //        once, by the lowest-id edge among those of its edges that are in F:
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kPeelBlock, MINB) k_peel(PeelArgs a) {
       alive = alive2;
       alive2 = t;
     }
-    compact = 8 * live <= 7 * nAlive;  // rewrite the list once an eighth of it is dead
+    compact = 4 * live <= 3 * nAlive;  // rewrite the list once a quarter of it is dead
     sc++;
     if (nF == 0) {
       if (live == 0) break;
